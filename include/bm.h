@@ -1,0 +1,181 @@
+/*
+ * bm.h -- C ABI of the GB300 (sm_103a) Self-Convolution block matcher.
+ *
+ * The operation (arXiv 2006.13714, "Exploiting Non-Local Priors via
+ * Self-Convolution"):
+ *
+ *   For every reference patch X_r and every candidate patch X_j whose
+ *   top-left corner lies in the search window of X_r, the squared distance
+ *     d(r, j) = ||X_j - X_r||_F^2                           (§III-A, Eq. equ:bm)
+ *             = ||X_j||^2 + ||X_r||^2 - 2 <X_r, X_j>        (§III-B, Lemma 2)
+ *   where <X_r, X_j> is the Self-Convolution C_r(j) of Eq. eq:selfConv
+ *   (restricted to the window as in the footnote to Eq. eq:unifySelfConv)
+ *   and ||X_j||^2 is a box filter of the squared image (the h_X (.) h_X
+ *   vector of §III-B).  Multi-channel patches sum the distance over
+ *   channels (§IV, S(.) in Eq. equ:self-convMM).  The output per reference
+ *   is the K candidates of smallest distance (Theorem 1: the l0 projection
+ *   of b = vec(C_r) - 0.5 h_X (.) h_X keeps the K largest entries).
+ *
+ * Geometry (readings of the paper, identical in the oracle):
+ *   - image: H x W x C, channels innermost, row-major, contiguous;
+ *   - candidate top-left grid G = [0, H-p] x [0, W-p];
+ *   - reference grid R = {(s*a, s*b)} in G, row-major;
+ *     n_ry = floor((H-p)/s) + 1, n_rx = floor((W-p)/s) + 1;
+ *   - window: top-left offsets dy, dx in [-h, h], h = (window-1)/2,
+ *     window odd, clipped to G (no padding, no shifting);
+ *   - order: distance ascending, then row-major offset y*W + x ascending;
+ *   - if the clipped window holds fewer than K candidates the tail of the
+ *     row is idx = -1, dist = INT32_MAX (uint8) / +inf (float32).
+ *
+ * Outputs: out_idx int32 [n_ry*n_rx][K] holds the candidate top-left as the
+ * row-major pixel offset y*W + x; out_dist is int32 (uint8 input, exact) or
+ * float32 (float32 input) of the same shape.
+ *
+ * Precision: uint8 distances are exact integers and the indices are
+ * bit-identical to the brute-force definition.  float32 distances are
+ * within 1e-4 relative of the exact (double) value; the K-set equals the
+ * exact one except for swaps among candidates whose exact distances differ
+ * by less than that tolerance.  Non-finite float32 pixels are not checked.
+ *
+ * Memory: every pointer named img / out_* in a device entry point is a
+ * device pointer owned by the caller; the library never frees it.  The
+ * library allocates its own workspace (inside the context's budget).
+ *
+ * Errors: every entry point returns a bm_status; nothing throws across the
+ * ABI.  On BM_ERR_INVALID / BM_ERR_UNSUPPORTED no kernel is launched and no
+ * output is written.  bm_last_error() returns the calling thread's last
+ * message for that context.
+ */
+#ifndef BM_H_
+#define BM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bm_ctx bm_ctx;
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* bm_stream;
+
+typedef enum { BM_U8 = 0, BM_F32 = 1 } bm_dtype;
+
+typedef enum {
+    BM_OK = 0,
+    BM_ERR_INVALID = -1,     /* bad argument; nothing launched            */
+    BM_ERR_UNSUPPORTED = -2, /* valid but not implemented (e.g. p*p*C>256)*/
+    BM_ERR_OOM = -3,         /* workspace exceeds the context budget      */
+    BM_ERR_CUDA = -4,        /* a CUDA call failed; see bm_last_error     */
+    BM_ERR_TIMEOUT = -5,     /* a bounded device wait ran out             */
+    BM_ERR_BUSY = -6,        /* request alone exceeds the budget          */
+    BM_ERR_NOT_FOUND = -7    /* unknown ticket                            */
+} bm_status;
+
+/* Algorithm selector for bm_set_algo. */
+typedef enum {
+    BM_ALGO_AUTO = 0,        /* tensor-core Self-Convolution when supported */
+    BM_ALGO_SELFCONV_TC = 1, /* tcgen05 cross term + box filter + top-K     */
+    BM_ALGO_DIRECT = 2       /* plain FP32 CUDA-core sum of (X_r - X_j)^2   */
+} bm_algo;
+
+/* One block-matching job; same fields as bm_match. */
+typedef struct {
+    const void* img;
+    int H, W, C;
+    bm_dtype dtype;
+    int patch, window, stride, K;
+    int32_t* out_idx;
+    void* out_dist;
+} bm_request;
+
+/* Counters accumulated over the context's life (host-read, best effort). */
+typedef struct {
+    uint64_t matches;         /* images matched                                  */
+    uint64_t refs;            /* reference patches matched                       */
+    uint64_t rerank_overflow; /* float32 refs whose boundary band left the pool  */
+    uint64_t fp64_rechecks;   /* float32 boundary ties re-ranked in FP64         */
+} bm_stats;
+
+/*
+ * Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * library's own device workspace (0 = 40 GiB).  tune_cache (nullable) is
+ * a file path where tuned tile choices are read from and written to.
+ * Returns BM_OK and *out, or an error (then *out is NULL).
+ */
+int bm_create(bm_ctx** out, int device, size_t mem_budget_bytes, const char* tune_cache);
+
+/* Destroy a context: drains its serving queue, frees its workspace. NULL is a no-op. */
+void bm_destroy(bm_ctx* ctx);
+
+/* Last error message of the calling thread for ctx ("" if none). Never NULL. */
+const char* bm_last_error(bm_ctx* ctx);
+
+/* Reference grid size, host only: n_ry = floor((H-p)/s)+1, n_rx likewise. */
+int bm_num_refs(int H, int W, int patch, int stride, int* n_ry, int* n_rx);
+
+/*
+ * K-nearest block matching of one image, asynchronous on `stream`
+ * (device pointers; see the file header for layout and conventions).
+ * Validation: 1 <= patch <= min(H, W); window odd >= 1; stride >= 1;
+ * 1 <= K <= 1024; 1 <= C <= 8; patch*patch*C <= 256 (else
+ * BM_ERR_UNSUPPORTED); non-null pointers.
+ */
+int bm_match(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
+             int patch, int window, int stride, int K,
+             int32_t* out_idx, void* out_dist, bm_stream stream);
+
+/*
+ * Same result through the plain FP32 CUDA-core direct-distance kernel
+ * (explicit sum of squared differences, Eq. equ:bmMetric_app): the
+ * comparison baseline.  Same arguments and conventions as bm_match.
+ */
+int bm_match_direct(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
+                    int patch, int window, int stride, int K,
+                    int32_t* out_idx, void* out_dist, bm_stream stream);
+
+/*
+ * Host-buffer variant: img, out_idx and out_dist are HOST pointers.  The
+ * call copies the image to the device, matches, copies the results back
+ * and returns after they have landed (synchronous).
+ */
+int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
+                  int patch, int window, int stride, int K,
+                  int32_t* out_idx, void* out_dist);
+
+/*
+ * Match n independent jobs (any mix of sizes, channel counts, dtypes and
+ * parameters) with one persistent launch per kernel stage, asynchronous on
+ * `stream`.  Same per-job conventions as bm_match.  Replays of an
+ * identical job list reuse a captured CUDA graph.
+ */
+int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream);
+
+/* Select the algorithm used by bm_match / bm_match_batch / bm_submit. */
+int bm_set_algo(bm_ctx* ctx, bm_algo algo);
+
+/*
+ * Serving: enqueue a request (the descriptor is copied, the buffers are
+ * not: they must stay alive until bm_poll reports done).  Requests are
+ * admitted under the memory budget as earlier ones finish and run
+ * concurrently on the context's streams.  BM_ERR_BUSY: the request alone
+ * exceeds the budget.  *ticket identifies it for bm_poll.
+ */
+int bm_submit(bm_ctx* ctx, const bm_request* req, uint64_t* ticket);
+
+/*
+ * Non-blocking completion check.  *done = 1 once the request finished;
+ * *status then holds its bm_status.  A ticket is released by the first
+ * poll that reports done.  Unknown ticket: BM_ERR_NOT_FOUND.
+ */
+int bm_poll(bm_ctx* ctx, uint64_t ticket, int* done, int* status);
+
+/* Read the context counters. */
+int bm_get_stats(bm_ctx* ctx, bm_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BM_H_ */

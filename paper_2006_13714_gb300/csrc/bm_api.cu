@@ -1,0 +1,544 @@
+// bm_api.cu -- host runtime and C ABI of the block-matching library.
+//
+// Context = one device, a device-memory budget for the library's own
+// workspace, a per-stream workspace cache, device counters, and a serving
+// loop (host thread) that admits submitted requests under the budget and
+// runs them concurrently on a small set of streams.
+#include "bm_internal.h"
+#include "../../include/bm.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace bm {
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, int K) {
+    if (H < 1 || W < 1 || C < 1 || C > kMaxC || p < 1 || p > H || p > W) return BM_ERR_INVALID;
+    if (win < 1 || (win % 2) == 0 || win > kMaxWindow || s < 1 || K < 1 || K > kMaxK)
+        return BM_ERR_INVALID;
+    if (dtype != kU8 && dtype != kF32) return BM_ERR_INVALID;
+    if ((long long)H * W >= (1ll << 31)) return BM_ERR_UNSUPPORTED;
+    if (p * p * C > kMaxPatchElems) return BM_ERR_UNSUPPORTED;
+    g.H = H; g.W = W; g.C = C; g.dtype = dtype;
+    g.p = p; g.win = win; g.h = (win - 1) / 2; g.s = s; g.K = K;
+    g.n_ry = (H - p) / s + 1;
+    g.n_rx = (W - p) / s + 1;
+    g.nR = g.n_ry * g.n_rx;
+    g.Hc = H - p + 1;
+    g.Wc = W - p + 1;
+    g.Cp = C == 1 ? 1 : C == 2 ? 2 : C <= 4 ? 4 : 8;
+    int elems = p * g.Cp;
+    g.pw = (elems + 7) / 8;
+    if (g.pw > 1 && (g.pw & 1)) g.pw += 1;
+    g.p_eff = g.pw == 1 ? round_up(p, 2) : p;
+    // plane rows: room for the widest staged strip beyond the right edge
+    g.plane_pitch = round_up(W * g.Cp + 8 * g.pw + 16, 8);
+    g.plane_rows = H + g.p_eff + 8;
+    g.L = dtype == kF32 ? std::min(kMaxK + 32, round_up(K + 16, 8)) : 0;
+    return BM_OK;
+}
+
+size_t plane_bytes(const Geom& g) { return (size_t)g.plane_rows * g.plane_pitch * 2; }
+size_t nrm_bytes(const Geom& g) { return (size_t)g.Hc * g.Wc * 4; }
+size_t pool_bytes(const Geom& g) { return g.dtype == kF32 ? (size_t)g.nR * g.L * 8 : 0; }
+
+bool tc_supported(const Geom& g);  // selfconv_tc.cu
+
+}  // namespace bm
+
+using namespace bm;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Ticket {
+    bm_request req;
+    int status = BM_OK;
+    bool admitted = false;
+    bool done = false;
+    size_t ws_bytes = 0;
+    int slot = -1;
+    void* ws = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Byte layout of one tensor-core job's workspace.
+struct WsLayout {
+    size_t plane0, plane1, nrm, pool_idx, pool_score, status, total;
+};
+
+WsLayout ws_layout(const Geom& g) {
+    WsLayout l{};
+    size_t off = 0;
+    l.plane0 = off; off += align256(plane_bytes(g));
+    l.plane1 = off; off += g.dtype == kF32 ? align256(plane_bytes(g)) : 0;
+    l.nrm = off; off += align256(nrm_bytes(g));
+    l.pool_idx = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
+    l.pool_score = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
+    l.status = off; off += 256;
+    l.total = off;
+    return l;
+}
+
+}  // namespace
+
+struct bm_ctx {
+    int device = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    std::string tune_cache;
+    bm_algo algo = BM_ALGO_AUTO;
+    std::mutex ws_mu;
+    std::unordered_map<cudaStream_t, Workspace> ws;  // per-stream cache
+    unsigned long long* d_counters = nullptr;        // [0] overflow, [1] fp64 rechecks
+    std::atomic<unsigned long long> matches{0}, refs{0};
+    // host-buffer path
+    std::mutex host_mu;
+    cudaStream_t host_stream = nullptr;
+    void* h_dev_img = nullptr; size_t h_dev_img_bytes = 0;
+    void* h_dev_out = nullptr; size_t h_dev_out_bytes = 0;
+    // serving
+    static constexpr int kSlots = 4;
+    cudaStream_t slot_stream[kSlots] = {};
+    int slot_busy[kSlots] = {};
+    std::mutex q_mu;
+    std::condition_variable q_cv;
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+    t_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(BM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int validate(const bm_request& r, Geom& g) {
+    int rc = make_geom(g, r.H, r.W, r.C, (int)r.dtype, r.patch, r.window, r.stride, r.K);
+    if (rc == BM_ERR_INVALID) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "invalid arguments: H=%d W=%d C=%d dtype=%d patch=%d window=%d stride=%d K=%d "
+                 "(need 1<=patch<=min(H,W), odd window<=%d, stride>=1, 1<=K<=%d, 1<=C<=%d)",
+                 r.H, r.W, r.C, (int)r.dtype, r.patch, r.window, r.stride, r.K, kMaxWindow,
+                 kMaxK, kMaxC);
+        return fail(rc, buf);
+    }
+    if (rc == BM_ERR_UNSUPPORTED)
+        return fail(rc, "unsupported: patch*patch*C must be <= 256 and H*W < 2^31");
+    if (!r.img || !r.out_idx || !r.out_dist) return fail(BM_ERR_INVALID, "null pointer argument");
+    return BM_OK;
+}
+
+bool use_tc(bm_ctx* ctx, const Geom& g) {
+    if (ctx->algo == BM_ALGO_DIRECT) return false;
+    return tc_supported(g);
+}
+
+size_t job_ws_bytes(bm_ctx* ctx, const Geom& g) {
+    return use_tc(ctx, g) ? ws_layout(g).total : 0;
+}
+
+// Enqueue the kernels of one job on st, using workspace ws (size job_ws_bytes).
+int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st) {
+    cudaError_t e;
+    if (!use_tc(ctx, g)) {
+        e = launch_direct(g, r.img, r.out_idx, r.out_dist, st);
+        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+        return BM_OK;
+    }
+    WsLayout l = ws_layout(g);
+    char* b = static_cast<char*>(ws);
+    uint16_t* p0 = reinterpret_cast<uint16_t*>(b + l.plane0);
+    uint16_t* p1 = g.dtype == kF32 ? reinterpret_cast<uint16_t*>(b + l.plane1) : nullptr;
+    void* nrm = b + l.nrm;
+    int* status = reinterpret_cast<int*>(b + l.status);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess)
+        return cuda_fail(e, "status reset");
+    if ((e = launch_planes(g, r.img, p0, p1, st)) != cudaSuccess)
+        return cuda_fail(e, "plane kernel launch");
+    if ((e = launch_boxfilter(g, r.img, nrm, st)) != cudaSuccess)
+        return cuda_fail(e, "box filter launch");
+    TcArgs a{};
+    a.plane0 = p0;
+    a.plane1 = p1;
+    a.nrm = nrm;
+    a.status = status;
+    if (g.dtype == kU8) {
+        a.out_idx = r.out_idx;
+        a.out_dist = static_cast<int32_t*>(r.out_dist);
+    } else {
+        a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
+        a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
+    }
+    if ((e = launch_tc(g, a, st)) != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
+    if (g.dtype == kF32) {
+        e = launch_rerank(g, static_cast<const float*>(r.img), static_cast<const float*>(nrm),
+                          a.pool_idx, a.pool_score, r.out_idx, static_cast<float*>(r.out_dist),
+                          ctx->d_counters, st);
+        if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
+    }
+    return BM_OK;
+}
+
+// Per-stream workspace of at least `bytes`, grown stream-ordered.
+int get_stream_ws(bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out) {
+    std::lock_guard<std::mutex> lk(ctx->ws_mu);
+    Workspace& w = ctx->ws[st];
+    if (w.bytes >= bytes) {
+        *out = w.ptr;
+        return BM_OK;
+    }
+    size_t others = ctx->used.load() - w.bytes;
+    if (others + bytes > ctx->budget)
+        return fail(BM_ERR_OOM, "workspace would exceed the context memory budget");
+    cudaError_t e;
+    if (w.ptr) {
+        if ((e = cudaFreeAsync(w.ptr, st)) != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+        ctx->used -= w.bytes;
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    if ((e = cudaMallocAsync(&w.ptr, bytes, st)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    w.bytes = bytes;
+    ctx->used += bytes;
+    *out = w.ptr;
+    return BM_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int match_common(bm_ctx* ctx, const bm_request& r, cudaStream_t st, bool force_direct) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    Geom g;
+    int rc = validate(r, g);
+    if (rc != BM_OK) return rc;
+    DeviceGuard dg(ctx->device);
+    bm_algo saved = ctx->algo;
+    if (force_direct) {
+        cudaError_t e = launch_direct(g, r.img, r.out_idx, r.out_dist, st);
+        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+    } else {
+        void* ws = nullptr;
+        size_t need = job_ws_bytes(ctx, g);
+        if (need) {
+            rc = get_stream_ws(ctx, st, need, &ws);
+            if (rc != BM_OK) return rc;
+        }
+        rc = enqueue_job(ctx, g, r, ws, st);
+        if (rc != BM_OK) return rc;
+    }
+    (void)saved;
+    ctx->matches += 1;
+    ctx->refs += (unsigned long long)g.nR;
+    return BM_OK;
+}
+
+// ---------------- serving loop ----------------
+
+void worker_loop(bm_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    while (true) {
+        // 1. retire finished requests
+        for (auto& kv : ctx->tickets) {
+            Ticket& t = kv.second;
+            if (!t.admitted || t.done) continue;
+            cudaError_t q = cudaEventQuery(t.ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess && t.status == BM_OK) {
+                t_last_error = std::string("request failed: ") + cudaGetErrorString(q);
+                t.status = BM_ERR_CUDA;
+            }
+            cudaEventDestroy(t.ev);
+            t.ev = nullptr;
+            ctx->used -= t.ws_bytes;
+            ctx->slot_busy[t.slot] -= 1;
+            t.done = true;
+        }
+        // 2. admit pending requests in arrival order while budget and a slot allow
+        while (!ctx->pending.empty()) {
+            uint64_t id = ctx->pending.front();
+            Ticket& t = ctx->tickets[id];
+            if (ctx->used.load() + t.ws_bytes > ctx->budget) break;
+            int slot = 0;
+            for (int s = 1; s < bm_ctx::kSlots; ++s)
+                if (ctx->slot_busy[s] < ctx->slot_busy[slot]) slot = s;
+            if (ctx->slot_busy[slot] >= 2) break;  // every stream already has two in flight
+            ctx->pending.pop_front();
+            cudaStream_t st = ctx->slot_stream[slot];
+            Geom g;
+            validate(t.req, g);
+            t.slot = slot;
+            t.admitted = true;
+            ctx->used += t.ws_bytes;
+            ctx->slot_busy[slot] += 1;
+            cudaError_t e = cudaSuccess;
+            if (t.ws_bytes) e = cudaMallocAsync(&t.ws, t.ws_bytes, st);
+            int rc = e == cudaSuccess ? enqueue_job(ctx, g, t.req, t.ws, st) : BM_ERR_OOM;
+            if (t.ws) cudaFreeAsync(t.ws, st);
+            t.ws = nullptr;
+            t.status = rc;
+            if (rc == BM_OK) {
+                ctx->matches += 1;
+                ctx->refs += (unsigned long long)g.nR;
+            }
+            cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
+            cudaEventRecord(t.ev, st);
+        }
+        if (ctx->stop) {
+            bool busy = false;
+            for (auto& kv : ctx->tickets) busy |= kv.second.admitted && !kv.second.done;
+            if (!busy && ctx->pending.empty()) break;
+        }
+        ctx->q_cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int bm_num_refs(int H, int W, int patch, int stride, int* n_ry, int* n_rx) {
+    if (H < 1 || W < 1 || patch < 1 || stride < 1 || patch > H || patch > W)
+        return fail(BM_ERR_INVALID, "invalid geometry");
+    if (n_ry) *n_ry = (H - patch) / stride + 1;
+    if (n_rx) *n_rx = (W - patch) / stride + 1;
+    return BM_OK;
+}
+
+int bm_create(bm_ctx** out, int device, size_t mem_budget_bytes, const char* tune_cache) {
+    if (!out) return fail(BM_ERR_INVALID, "null output pointer");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(BM_ERR_INVALID, "no such CUDA device");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(BM_ERR_UNSUPPORTED, std::string("library is built for sm_103a, device is ") +
+                                            prop.name);
+    bm_ctx* ctx = new bm_ctx();
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)40 << 30;
+    if (tune_cache) ctx->tune_cache = tune_cache;
+    DeviceGuard dg(device);
+    if ((e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(e, "context setup");
+    }
+    for (int s = 0; s < bm_ctx::kSlots; ++s) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->slot_stream[s], cudaStreamNonBlocking)) !=
+            cudaSuccess) {
+            delete ctx;
+            return cuda_fail(e, "stream create");
+        }
+    }
+    ctx->worker = std::thread(worker_loop, ctx);
+    *out = ctx;
+    return BM_OK;
+}
+
+void bm_destroy(bm_ctx* ctx) {
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        ctx->stop = true;
+    }
+    ctx->q_cv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->ws)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    if (ctx->h_dev_img) cudaFree(ctx->h_dev_img);
+    if (ctx->h_dev_out) cudaFree(ctx->h_dev_out);
+    if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    for (int s = 0; s < bm_ctx::kSlots; ++s)
+        if (ctx->slot_stream[s]) cudaStreamDestroy(ctx->slot_stream[s]);
+    delete ctx;
+}
+
+const char* bm_last_error(bm_ctx*) { return t_last_error.c_str(); }
+
+int bm_set_algo(bm_ctx* ctx, bm_algo algo) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    if (algo != BM_ALGO_AUTO && algo != BM_ALGO_SELFCONV_TC && algo != BM_ALGO_DIRECT)
+        return fail(BM_ERR_INVALID, "unknown algorithm");
+    ctx->algo = algo;
+    return BM_OK;
+}
+
+int bm_match(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+             int window, int stride, int K, int32_t* out_idx, void* out_dist, bm_stream stream) {
+    bm_request r{img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist};
+    return match_common(ctx, r, reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+int bm_match_direct(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                    int window, int stride, int K, int32_t* out_idx, void* out_dist,
+                    bm_stream stream) {
+    bm_request r{img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist};
+    return match_common(ctx, r, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                  int window, int stride, int K, int32_t* out_idx, void* out_dist) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    bm_request r{img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist};
+    Geom g;
+    int rc = validate(r, g);
+    if (rc != BM_OK) return rc;
+    std::lock_guard<std::mutex> lk(ctx->host_mu);
+    DeviceGuard dg(ctx->device);
+    size_t img_bytes = (size_t)H * W * C * (dtype == BM_U8 ? 1 : 4);
+    size_t out_bytes = (size_t)g.nR * K * 8;
+    cudaError_t e;
+    if (ctx->h_dev_img_bytes < img_bytes) {
+        if (ctx->h_dev_img) cudaFree(ctx->h_dev_img);
+        ctx->h_dev_img = nullptr;
+        ctx->h_dev_img_bytes = 0;
+        if ((e = cudaMalloc(&ctx->h_dev_img, img_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        ctx->h_dev_img_bytes = img_bytes;
+    }
+    if (ctx->h_dev_out_bytes < out_bytes) {
+        if (ctx->h_dev_out) cudaFree(ctx->h_dev_out);
+        ctx->h_dev_out = nullptr;
+        ctx->h_dev_out_bytes = 0;
+        if ((e = cudaMalloc(&ctx->h_dev_out, out_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        ctx->h_dev_out_bytes = out_bytes;
+    }
+    cudaStream_t st = ctx->host_stream;
+    int32_t* d_idx = static_cast<int32_t*>(ctx->h_dev_out);
+    void* d_dist = static_cast<char*>(ctx->h_dev_out) + (size_t)g.nR * K * 4;
+    if ((e = cudaMemcpyAsync(ctx->h_dev_img, img, img_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "host-to-device copy");
+    bm_request dr{ctx->h_dev_img, H, W, C, dtype, patch, window, stride, K, d_idx, d_dist};
+    rc = match_common(ctx, dr, st, false);
+    if (rc != BM_OK) return rc;
+    if ((e = cudaMemcpyAsync(out_idx, d_idx, (size_t)g.nR * K * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_dist, d_dist, (size_t)g.nR * K * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    return BM_OK;
+}
+
+int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    if (n < 0 || (n > 0 && !reqs)) return fail(BM_ERR_INVALID, "bad request list");
+    std::vector<Geom> gs(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(reqs[i], gs[i]);
+        if (rc != BM_OK) return rc;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DeviceGuard dg(ctx->device);
+    // one workspace holding every job's region
+    std::vector<size_t> offs(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        offs[i] = total;
+        total += align256(job_ws_bytes(ctx, gs[i]));
+    }
+    void* ws = nullptr;
+    if (total) {
+        int rc = get_stream_ws(ctx, st, total, &ws);
+        if (rc != BM_OK) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = enqueue_job(ctx, gs[i], reqs[i], static_cast<char*>(ws) + offs[i], st);
+        if (rc != BM_OK) return rc;
+        ctx->matches += 1;
+        ctx->refs += (unsigned long long)gs[i].nR;
+    }
+    return BM_OK;
+}
+
+int bm_submit(bm_ctx* ctx, const bm_request* req, uint64_t* ticket) {
+    if (!ctx || !req || !ticket) return fail(BM_ERR_INVALID, "null argument");
+    Geom g;
+    int rc = validate(*req, g);
+    if (rc != BM_OK) return rc;
+    size_t need = job_ws_bytes(ctx, g);
+    if (need > ctx->budget) return fail(BM_ERR_BUSY, "request alone exceeds the memory budget");
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    if (ctx->stop) return fail(BM_ERR_INVALID, "context is shutting down");
+    uint64_t id = ctx->next_ticket++;
+    Ticket& t = ctx->tickets[id];
+    t.req = *req;
+    t.ws_bytes = need;
+    ctx->pending.push_back(id);
+    *ticket = id;
+    ctx->q_cv.notify_all();
+    return BM_OK;
+}
+
+int bm_poll(bm_ctx* ctx, uint64_t ticket, int* done, int* status) {
+    if (!ctx || !done || !status) return fail(BM_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(BM_ERR_NOT_FOUND, "unknown ticket");
+    *done = it->second.done ? 1 : 0;
+    *status = it->second.status;
+    if (it->second.done) ctx->tickets.erase(it);
+    return BM_OK;
+}
+
+int bm_get_stats(bm_ctx* ctx, bm_stats* out) {
+    if (!ctx || !out) return fail(BM_ERR_INVALID, "null argument");
+    DeviceGuard dg(ctx->device);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "counter read");
+    out->matches = ctx->matches.load();
+    out->refs = ctx->refs.load();
+    out->rerank_overflow = c[0];
+    out->fp64_rechecks = c[1];
+    return BM_OK;
+}
+
+}  // extern "C"

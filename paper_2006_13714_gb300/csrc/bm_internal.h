@@ -1,0 +1,81 @@
+// bm_internal.h -- shared declarations of the CUDA block-matching library.
+//
+// Geometry of one job (readings shared with the public header bm.h):
+//   image H x W x C (HWC, row-major); patch p; stride s; window 2h+1;
+//   candidate top-left grid G = [0, H-p] x [0, W-p];
+//   reference grid R = {(s*a, s*b)} in G; n_ry = (H-p)/s + 1, n_rx = (W-p)/s + 1.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bm {
+
+constexpr int kMaxK = 128;        // largest K served
+constexpr int kMaxPatchElems = 256;  // p*p*C limit of every kernel
+constexpr int kMaxWindow = 127;   // largest odd window
+constexpr int kMaxC = 8;
+
+enum DType : int { kU8 = 0, kF32 = 1 };
+
+struct Geom {
+    int H, W, C, dtype;
+    int p, win, h, s, K;
+    int n_ry, n_rx, nR;
+    int Hc, Wc;          // candidate grid extent: H-p+1, W-p+1
+    // bf16 operand planes (tensor-core path)
+    int Cp;              // channels padded to 1, 2, 4 or 8
+    int pw;              // 16-byte chunks per patch row, even unless 1
+    int p_eff;           // patch rows fed to the MMA (p, rounded up to even if pw == 1)
+    int plane_pitch;     // elements per plane row (multiple of 8)
+    int plane_rows;      // rows per plane (H + padding)
+    int L;               // float32 candidate pool per reference
+};
+
+// Fill g from the arguments; returns 0 or a negative bm_status.
+int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, int K);
+
+// Workspace byte counts of one job (tensor-core path).
+size_t plane_bytes(const Geom& g);       // one bf16 plane
+size_t nrm_bytes(const Geom& g);         // candidate norms
+size_t pool_bytes(const Geom& g);        // float32 candidate pool
+
+// ---- kernels (each launcher returns cudaGetLastError()) ----
+
+// (a1) box filter of the squared image: nrm[y][x] = sum_{u,v<p, c<C} X[y+u][x+v][c]^2
+//      int32 (uint8, exact) or float32 (float32, compensated summation).
+cudaError_t launch_boxfilter(const Geom& g, const void* img, void* nrm, cudaStream_t st);
+
+// bf16 operand planes: uint8 -> one exact plane; float32 -> hi and lo planes
+// with x ~= hi + lo (hi = RN_bf16(x), lo = RN_bf16(x - hi)).
+cudaError_t launch_planes(const Geom& g, const void* img, uint16_t* plane0, uint16_t* plane1,
+                          cudaStream_t st);
+
+// Plain FP32 CUDA-core direct-distance block matcher (comparison baseline).
+cudaError_t launch_direct(const Geom& g, const void* img, int32_t* out_idx, void* out_dist,
+                          cudaStream_t st);
+
+// (a3-a5) tensor-core cross term + distance assembly + top-K.
+// uint8: writes the final out_idx / out_dist.  float32: writes the candidate
+// pool (pool_idx, pool_score) of L entries per reference.
+struct TcArgs {
+    const uint16_t* plane0;   // bf16 hi (or exact uint8) plane
+    const uint16_t* plane1;   // bf16 lo plane (float32 only)
+    const void* nrm;          // int32 or float32 norms [Hc][Wc]
+    int32_t* out_idx;         // uint8: final indices
+    int32_t* out_dist;        // uint8: final distances
+    int32_t* pool_idx;        // float32: candidate pool offsets [nR][L]
+    float* pool_score;        // float32: candidate pool scores  [nR][L]
+    int* status;              // device error word (0 = ok)
+};
+cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
+
+// (a6) float32 boundary re-rank: direct recomputation of the pool's band,
+// FP64 only for ties at the K-th boundary; writes the final outputs.
+cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
+                          const int32_t* pool_idx, const float* pool_score,
+                          int32_t* out_idx, float* out_dist, unsigned long long* counters,
+                          cudaStream_t st);
+
+}  // namespace bm

@@ -1,0 +1,58 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol that
+include/*.h declares, and its host-only helpers behave.  No compute calls."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2006_13714_gb300 import bm as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(?:int|void|const char\s*\*)\s+(bm_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bm_create", "bm_match", "bm_submit", "bm_poll", "bm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.build_ext.build())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("H,W,p,s,want", [
+    (64, 64, 8, 1, (57, 57)), (512, 512, 8, 3, (169, 169)), (1024, 1024, 8, 3, (339, 339)),
+    (321, 481, 7, 4, (79, 119)), (8, 8, 8, 5, (1, 1))])
+def test_num_refs(H, W, p, s, want):
+    assert B.bm_num_refs(H, W, p, s) == want
+
+
+@pytest.mark.parametrize("args", [(8, 8, 9, 1), (8, 8, 0, 1), (8, 8, 2, 0), (0, 8, 1, 1)])
+def test_num_refs_rejects(args):
+    with pytest.raises(B.BMError) as e:
+        B.bm_num_refs(*args)
+    assert e.value.code == B.BM_ERR_INVALID
+
+
+def test_create_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(B.BMError) as e:
+        B.bm_create(0)
+    assert e.value.code in (B.BM_ERR_CUDA, B.BM_ERR_INVALID)

@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Small cases are compared in full (several tiles plus ragged tails); the
+full-size workloads are compared on a seeded sample of references that
+always includes the grid corners and edges.
+"""
+import numpy as np
+import pytest
+
+from paper_2006_13714_gb300 import bm as B
+from paper_2006_13714_gb300 import synth
+from parity import compare, sample_refs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def make_image(H, W, C, dtype, seed, sigma=25.0):
+    if C == 1:
+        return synth.gray(H, W, sigma, seed, np.uint8 if dtype == "u8" else np.float32)
+    if C == 4 and dtype == "u8":
+        return synth.rgbnir(H, W, sigma, seed)
+    planes = [synth.gray(H, W, sigma, seed * 10 + c, np.uint8 if dtype == "u8" else np.float32)
+              for c in range(C)]
+    return np.ascontiguousarray(np.stack(planes, axis=-1))
+
+
+def run(ctx, img, p, win, s, K, algo):
+    t = torch.from_numpy(img).cuda()
+    fn = ctx.match if algo == "selfconv" else ctx.match_direct
+    idx, dist = fn(t, p, win, s, K)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), dist.cpu().numpy()
+
+
+SMALL = [
+    # id,             H,   W,  C, dtype, p, win, s,  K
+    ("cfg1_tiny",     64,  64, 1, "u8",  8, 21, 1, 16),
+    ("cfg2_small",    96,  88, 1, "f32", 8, 39, 3, 16),
+    ("cfg3_small",   150, 133, 1, "f32", 7, 61, 4, 70),
+    ("cfg4_small",    80,  72, 4, "u8",  8, 39, 3, 32),
+    ("cfg4_small_f",  70,  66, 4, "f32", 8, 39, 3, 32),
+    ("ragged_u8",     45,  77, 1, "u8",  5,  9, 2, 10),
+    ("c2_u8",         40,  50, 2, "u8",  6, 11, 2, 12),
+    ("c3_f32",        37,  41, 3, "f32", 4,  7, 1,  8),
+    ("p1_fullwin",    20,  30, 1, "u8",  1,  5, 1, 25),
+    ("win1_pad",      20,  20, 1, "f32", 3,  1, 2,  4),
+    ("k_gt_window",   30,  30, 1, "u8",  4,  5, 3, 40),
+    ("p_eq_H",         8,  12, 1, "u8",  8,  7, 1,  5),
+    ("p7_c4",         60,  50, 4, "u8",  7, 15, 3, 20),
+    ("p16_f32",       50,  50, 1, "f32", 16, 9, 4,  8),
+    ("stride5_f32",  101, 203, 1, "f32", 8, 39, 5, 16),
+    ("tall_u8",      300,  40, 1, "u8",  8, 39, 3, 16),
+]
+
+
+@pytest.mark.parametrize("algo", ["selfconv", "direct"])
+@pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
+def test_small_full_parity(ctx, case, algo):
+    name, H, W, C, dt, p, win, s, K = case
+    img = make_image(H, W, C, dt, seed=abs(hash(name)) % 10007)
+    gidx, gdist = run(ctx, img, p, win, s, K, algo)
+    compare(img, p, win, s, K, gidx, gdist)
+
+
+@pytest.mark.parametrize("algo", ["selfconv", "direct"])
+@pytest.mark.parametrize("dt", ["u8", "f32"])
+def test_constant_image_tie_break(ctx, algo, dt):
+    img = np.full((40, 37), 77, dtype=np.uint8 if dt == "u8" else np.float32)
+    gidx, gdist = run(ctx, img, 6, 9, 2, 30, algo)
+    compare(img, 6, 9, 2, 30, gidx, gdist)
+
+
+FULL = [
+    ("cfg2_512_f32", 512, 512, 1, "f32", 8, 39, 3, 16, 2000),
+    ("cfg4_1024x4_u8", 1024, 1024, 4, "u8", 8, 39, 3, 32, 4000),
+    ("cfg3_1024_f32", 1024, 1024, 1, "f32", 7, 61, 4, 70, 3000),
+    ("cfg1_64_u8", 64, 64, 1, "u8", 8, 21, 1, 16, 1000),
+]
+
+
+@pytest.mark.parametrize("algo", ["selfconv", "direct"])
+@pytest.mark.parametrize("case", FULL, ids=[c[0] for c in FULL])
+def test_full_size_sampled_parity(ctx, case, algo):
+    name, H, W, C, dt, p, win, s, K, seed = case
+    img = make_image(H, W, C, dt, seed=seed, sigma=20.0 if C == 4 else 25.0)
+    gidx, gdist = run(ctx, img, p, win, s, K, algo)
+    ny, nx = B.bm_num_refs(H, W, p, s)
+    refs = sample_refs(ny, nx, 300, seed)
+    compare(img, p, win, s, K, gidx, gdist, refs=refs)
+
+
+def test_selfconv_equals_direct_bitwise_on_u8(ctx):
+    img = make_image(200, 180, 1, "u8", seed=5)
+    a = run(ctx, img, 8, 39, 3, 16, "selfconv")
+    b = run(ctx, img, 8, 39, 3, 16, "direct")
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("bad", [
+    dict(p=0), dict(p=70), dict(win=4), dict(win=129), dict(s=0), dict(K=0), dict(K=129),
+])
+def test_invalid_arguments_write_nothing(ctx, bad):
+    img = torch.from_numpy(make_image(64, 64, 1, "u8", seed=1)).cuda()
+    args = dict(p=8, win=21, s=1, K=16)
+    args.update(bad)
+    idx = torch.full((57 * 57, 16), -7, dtype=torch.int32, device="cuda")
+    dist = torch.full((57 * 57, 16), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(B.BMError) as e:
+        ctx.match(img, args["p"], args["win"], args["s"], args["K"], out=(idx, dist))
+    assert e.value.code == B.BM_ERR_INVALID
+    torch.cuda.synchronize()
+    assert bool((idx == -7).all()) and bool((dist == -7).all())
+
+
+def test_unsupported_patch_volume(ctx):
+    img = torch.zeros((64, 64, 8), dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.BMError) as e:
+        ctx.match(img, 8, 5, 4, 4)
+    assert e.value.code == B.BM_ERR_UNSUPPORTED
+
+
+def test_host_path_equals_device_path(ctx):
+    for dt in ("u8", "f32"):
+        img = make_image(130, 120, 1, dt, seed=12)
+        hidx, hdist = ctx.match_host(img, 8, 39, 3, 16)
+        didx, ddist = run(ctx, img, 8, 39, 3, 16, "selfconv")
+        assert np.array_equal(hidx, didx) and np.array_equal(hdist, ddist)
+
+
+def test_batch_equals_single(ctx):
+    specs = [(100, 90, 1, "f32", 8, 39, 3, 16), (64, 64, 1, "u8", 8, 21, 1, 16),
+             (80, 72, 4, "u8", 8, 39, 3, 32), (150, 133, 1, "f32", 7, 61, 4, 70)]
+    imgs, reqs, outs = [], [], []
+    for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
+        t = torch.from_numpy(make_image(H, W, C, dt, seed=70 + i)).cuda()
+        idx, dist = ctx.outputs(t, p, s, K)
+        imgs.append(t)
+        outs.append((idx, dist))
+        reqs.append(B.Context.request(t, p, win, s, K, idx, dist))
+    ctx.match_batch(reqs)
+    torch.cuda.synchronize()
+    for (H, W, C, dt, p, win, s, K), t, (idx, dist) in zip(specs, imgs, outs):
+        a, b = ctx.match(t, p, win, s, K)
+        torch.cuda.synchronize()
+        assert torch.equal(a, idx) and torch.equal(b, dist)
