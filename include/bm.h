@@ -96,6 +96,8 @@ typedef struct {
     uint64_t refs;            /* reference patches matched                       */
     uint64_t rerank_overflow; /* float32 refs whose boundary band left the pool  */
     uint64_t fp64_rechecks;   /* float32 boundary ties re-ranked in FP64         */
+    uint64_t bound_violations;/* float32 pool entries outside the stated error bound (expected 0) */
+    uint64_t tc_jobs;         /* images matched on the tensor-core path          */
 } bm_stats;
 
 /*
@@ -118,9 +120,10 @@ int bm_num_refs(int H, int W, int patch, int stride, int* n_ry, int* n_rx);
 /*
  * K-nearest block matching of one image, asynchronous on `stream`
  * (device pointers; see the file header for layout and conventions).
- * Validation: 1 <= patch <= min(H, W); window odd >= 1; stride >= 1;
- * 1 <= K <= 1024; 1 <= C <= 8; patch*patch*C <= 256 (else
- * BM_ERR_UNSUPPORTED); non-null pointers.
+ * Validation: 1 <= patch <= min(H, W); window odd, 1 <= window <= 127;
+ * stride >= 1; 1 <= K <= 128; 1 <= C <= 8; non-null pointers (else
+ * BM_ERR_INVALID); patch*patch*C <= 256 and H*W < 2^31 (else
+ * BM_ERR_UNSUPPORTED).
  */
 int bm_match(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
              int patch, int window, int stride, int K,
@@ -173,6 +176,30 @@ int bm_poll(bm_ctx* ctx, uint64_t ticket, int* done, int* status);
 
 /* Read the context counters. */
 int bm_get_stats(bm_ctx* ctx, bm_stats* out);
+
+/* Kernel stages timed by bm_set_timing. */
+enum {
+    BM_STAGE_PLANES = 0, /* bf16 operand planes                          */
+    BM_STAGE_BOX = 1,    /* (a1) box filter of the squared image         */
+    BM_STAGE_TC = 2,     /* (a3-a5) tensor-core cross term + top-K       */
+    BM_STAGE_RERANK = 3, /* (a6) float32 boundary re-rank                */
+    BM_STAGE_DIRECT = 4, /* plain FP32 direct-distance kernel            */
+    BM_NUM_STAGES = 5
+};
+
+typedef struct {
+    uint64_t launches[BM_NUM_STAGES]; /* kernel launches timed per stage */
+    double ms[BM_NUM_STAGES];         /* summed device time per stage    */
+} bm_timing;
+
+/*
+ * Stage timing: while enabled, every kernel launch of the context is
+ * bracketed by CUDA events on its own stream.  bm_get_timing waits for the
+ * recorded events, adds their elapsed times into *out (accumulated since
+ * the last reset) and, if reset != 0, clears the totals.
+ */
+int bm_set_timing(bm_ctx* ctx, int enable);
+int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,16 @@ class bm_request(ctypes.Structure):
 
 class bm_stats(ctypes.Structure):
     _fields_ = [("matches", ctypes.c_uint64), ("refs", ctypes.c_uint64),
-                ("rerank_overflow", ctypes.c_uint64), ("fp64_rechecks", ctypes.c_uint64)]
+                ("rerank_overflow", ctypes.c_uint64), ("fp64_rechecks", ctypes.c_uint64),
+                ("bound_violations", ctypes.c_uint64), ("tc_jobs", ctypes.c_uint64)]
+
+
+NUM_STAGES = 5
+STAGES = ("planes", "box", "tc", "rerank", "direct")
+
+
+class bm_timing(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * NUM_STAGES), ("ms", ctypes.c_double * NUM_STAGES)]
 
 
 def library_path() -> str:
@@ -74,6 +83,8 @@ def load(build_if_missing: bool = True):
             "bm_submit": ([vp, ctypes.POINTER(bm_request), ctypes.POINTER(ctypes.c_uint64)], ci),
             "bm_poll": ([vp, ctypes.c_uint64, pi, pi], ci),
             "bm_get_stats": ([vp, ctypes.POINTER(bm_stats)], ci),
+            "bm_set_timing": ([vp, ci], ci),
+            "bm_get_timing": ([vp, ctypes.POINTER(bm_timing), ci], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -153,6 +164,19 @@ def bm_get_stats(ctx) -> dict:
     if rc != BM_OK:
         raise BMError(rc, bm_last_error(ctx))
     return {k: int(getattr(s, k)) for k, _ in bm_stats._fields_}
+
+
+def bm_set_timing(ctx, enable: int) -> int:
+    return load().bm_set_timing(ctx, enable)
+
+
+def bm_get_timing(ctx, reset: int = 0) -> dict:
+    t = bm_timing()
+    rc = load().bm_get_timing(ctx, ctypes.byref(t), reset)
+    if rc != BM_OK:
+        raise BMError(rc, bm_last_error(ctx))
+    return {name: {"launches": int(t.launches[i]), "ms": float(t.ms[i])}
+            for i, name in enumerate(STAGES)}
 
 
 # ---- torch convenience wrapper ----
@@ -277,3 +301,9 @@ class Context:
 
     def stats(self) -> dict:
         return bm_get_stats(self.handle)
+
+    def set_timing(self, enable: bool):
+        self._check(bm_set_timing(self.handle, 1 if enable else 0))
+
+    def timing(self, reset: bool = False) -> dict:
+        return bm_get_timing(self.handle, 1 if reset else 0)

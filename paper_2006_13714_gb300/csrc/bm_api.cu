@@ -46,7 +46,7 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
     // plane rows: room for the widest staged strip beyond the right edge
     g.plane_pitch = round_up(W * g.Cp + 8 * g.pw + 16, 8);
     g.plane_rows = H + g.p_eff + 8;
-    g.L = dtype == kF32 ? std::min(kMaxK + 32, round_up(K + 16, 8)) : 0;
+    g.L = dtype == kF32 ? std::min(176, round_up(K + 48, 8)) : 0;
     return BM_OK;
 }
 
@@ -111,7 +111,13 @@ struct bm_ctx {
     std::mutex ws_mu;
     std::unordered_map<cudaStream_t, Workspace> ws;  // per-stream cache
     unsigned long long* d_counters = nullptr;        // [0] overflow, [1] fp64 rechecks
-    std::atomic<unsigned long long> matches{0}, refs{0};
+    std::atomic<unsigned long long> matches{0}, refs{0}, tc_jobs{0};
+    // stage timing
+    std::atomic<int> timing{0};
+    std::mutex tm_mu;
+    struct EvPair { int stage; cudaEvent_t a, b; };
+    std::vector<EvPair> tm_pending;
+    bm_timing tm_total{};
     // host-buffer path
     std::mutex host_mu;
     cudaStream_t host_stream = nullptr;
@@ -167,11 +173,27 @@ size_t job_ws_bytes(bm_ctx* ctx, const Geom& g) {
     return use_tc(ctx, g) ? ws_layout(g).total : 0;
 }
 
+// Run `launch` on st; with stage timing on, bracket it with two events.
+template <class F>
+cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch) {
+    if (!ctx->timing.load()) return launch();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(ctx->tm_mu);
+    ctx->tm_pending.push_back({stage, a, b});
+    return e;
+}
+
 // Enqueue the kernels of one job on st, using workspace ws (size job_ws_bytes).
 int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st) {
     cudaError_t e;
     if (!use_tc(ctx, g)) {
-        e = launch_direct(g, r.img, r.out_idx, r.out_dist, st);
+        e = timed(ctx, BM_STAGE_DIRECT, st,
+                  [&] { return launch_direct(g, r.img, r.out_idx, r.out_dist, st); });
         if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
         return BM_OK;
     }
@@ -183,9 +205,11 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
     int* status = reinterpret_cast<int*>(b + l.status);
     if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess)
         return cuda_fail(e, "status reset");
-    if ((e = launch_planes(g, r.img, p0, p1, st)) != cudaSuccess)
+    if ((e = timed(ctx, BM_STAGE_PLANES, st,
+                   [&] { return launch_planes(g, r.img, p0, p1, st); })) != cudaSuccess)
         return cuda_fail(e, "plane kernel launch");
-    if ((e = launch_boxfilter(g, r.img, nrm, st)) != cudaSuccess)
+    if ((e = timed(ctx, BM_STAGE_BOX, st,
+                   [&] { return launch_boxfilter(g, r.img, nrm, st); })) != cudaSuccess)
         return cuda_fail(e, "box filter launch");
     TcArgs a{};
     a.plane0 = p0;
@@ -199,11 +223,15 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
         a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
         a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
     }
-    if ((e = launch_tc(g, a, st)) != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
+    if ((e = timed(ctx, BM_STAGE_TC, st, [&] { return launch_tc(g, a, st); })) != cudaSuccess)
+        return cuda_fail(e, "tensor-core kernel launch");
+    ctx->tc_jobs += 1;
     if (g.dtype == kF32) {
-        e = launch_rerank(g, static_cast<const float*>(r.img), static_cast<const float*>(nrm),
-                          a.pool_idx, a.pool_score, r.out_idx, static_cast<float*>(r.out_dist),
-                          ctx->d_counters, st);
+        e = timed(ctx, BM_STAGE_RERANK, st, [&] {
+            return launch_rerank(g, static_cast<const float*>(r.img), static_cast<const float*>(nrm),
+                                 a.pool_idx, a.pool_score, r.out_idx,
+                                 static_cast<float*>(r.out_dist), ctx->d_counters, st);
+        });
         if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
     }
     return BM_OK;
@@ -253,9 +281,9 @@ int match_common(bm_ctx* ctx, const bm_request& r, cudaStream_t st, bool force_d
     int rc = validate(r, g);
     if (rc != BM_OK) return rc;
     DeviceGuard dg(ctx->device);
-    bm_algo saved = ctx->algo;
     if (force_direct) {
-        cudaError_t e = launch_direct(g, r.img, r.out_idx, r.out_dist, st);
+        cudaError_t e = timed(ctx, BM_STAGE_DIRECT, st,
+                              [&] { return launch_direct(g, r.img, r.out_idx, r.out_dist, st); });
         if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
     } else {
         void* ws = nullptr;
@@ -267,7 +295,6 @@ int match_common(bm_ctx* ctx, const bm_request& r, cudaStream_t st, bool force_d
         rc = enqueue_job(ctx, g, r, ws, st);
         if (rc != BM_OK) return rc;
     }
-    (void)saved;
     ctx->matches += 1;
     ctx->refs += (unsigned long long)g.nR;
     return BM_OK;
@@ -538,7 +565,36 @@ int bm_get_stats(bm_ctx* ctx, bm_stats* out) {
     out->refs = ctx->refs.load();
     out->rerank_overflow = c[0];
     out->fp64_rechecks = c[1];
+    out->bound_violations = c[2];
+    out->tc_jobs = ctx->tc_jobs.load();
     return BM_OK;
+}
+
+int bm_set_timing(bm_ctx* ctx, int enable) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    ctx->timing = enable ? 1 : 0;
+    return BM_OK;
+}
+
+int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset) {
+    if (!ctx || !out) return fail(BM_ERR_INVALID, "null argument");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->tm_mu);
+    int rc = BM_OK;
+    for (auto& ev : ctx->tm_pending) {
+        cudaError_t e = cudaEventSynchronize(ev.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.a, ev.b);
+        if (e != cudaSuccess && rc == BM_OK) rc = cuda_fail(e, "timing event");
+        ctx->tm_total.launches[ev.stage] += 1;
+        ctx->tm_total.ms[ev.stage] += ms;
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    ctx->tm_pending.clear();
+    *out = ctx->tm_total;
+    if (reset) ctx->tm_total = bm_timing{};
+    return rc;
 }
 
 }  // extern "C"

@@ -4,6 +4,8 @@ Small cases are compared in full (several tiles plus ragged tails); the
 full-size workloads are compared on a seeded sample of references that
 always includes the grid corners and edges.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -67,7 +69,7 @@ SMALL = [
 @pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
 def test_small_full_parity(ctx, case, algo):
     name, H, W, C, dt, p, win, s, K = case
-    img = make_image(H, W, C, dt, seed=abs(hash(name)) % 10007)
+    img = make_image(H, W, C, dt, seed=zlib.crc32(name.encode()) % 10007)
     gidx, gdist = run(ctx, img, p, win, s, K, algo)
     compare(img, p, win, s, K, gidx, gdist)
 
@@ -153,3 +155,23 @@ def test_batch_equals_single(ctx):
         a, b = ctx.match(t, p, win, s, K)
         torch.cuda.synchronize()
         assert torch.equal(a, idx) and torch.equal(b, dist)
+
+
+TC_CASES = [("cfg1", 64, 64, 1, "u8", 8, 21, 1, 16), ("cfg2", 96, 88, 1, "f32", 8, 39, 3, 16),
+            ("cfg3", 150, 133, 1, "f32", 7, 61, 4, 70), ("cfg4", 80, 72, 4, "u8", 8, 39, 3, 32)]
+
+
+@pytest.mark.parametrize("case", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tensor_core_path_is_used(ctx, case):
+    name, H, W, C, dt, p, win, s, K = case
+    before = ctx.stats()["tc_jobs"]
+    run(ctx, make_image(H, W, C, dt, seed=3), p, win, s, K, "selfconv")
+    assert ctx.stats()["tc_jobs"] == before + 1
+
+
+def test_float_error_bound_never_violated(ctx):
+    # every float32 pool entry's identity estimate stays inside eps (n_r + n_j)
+    for i, (H, W, p, win, s, K) in enumerate([(200, 180, 8, 39, 3, 16), (160, 150, 7, 61, 4, 70)]):
+        run(ctx, make_image(H, W, 1, "f32", seed=40 + i), p, win, s, K, "selfconv")
+    st = ctx.stats()
+    assert st["bound_violations"] == 0, st
