@@ -46,7 +46,7 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
     // plane rows: room for the widest staged strip beyond the right edge
     g.plane_pitch = round_up(W * g.Cp + 8 * g.pw + 16, 8);
     g.plane_rows = H + g.p_eff + 8;
-    g.L = dtype == kF32 ? std::min(176, round_up(K + 48, 8)) : 0;
+    g.L = dtype == kF32 ? std::min(160, round_up(K + 16, 8)) : 0;
     return BM_OK;
 }
 
@@ -203,13 +203,17 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
     uint16_t* p1 = g.dtype == kF32 ? reinterpret_cast<uint16_t*>(b + l.plane1) : nullptr;
     void* nrm = b + l.nrm;
     int* status = reinterpret_cast<int*>(b + l.status);
+    float* center = reinterpret_cast<float*>(b + l.status + 16);
     if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess)
         return cuda_fail(e, "status reset");
     if ((e = timed(ctx, BM_STAGE_PLANES, st,
-                   [&] { return launch_planes(g, r.img, p0, p1, st); })) != cudaSuccess)
+                   [&] { return launch_center(g, r.img, center, st); })) != cudaSuccess)
+        return cuda_fail(e, "centre kernel launch");
+    if ((e = timed(ctx, BM_STAGE_PLANES, st,
+                   [&] { return launch_planes(g, r.img, center, p0, p1, st); })) != cudaSuccess)
         return cuda_fail(e, "plane kernel launch");
     if ((e = timed(ctx, BM_STAGE_BOX, st,
-                   [&] { return launch_boxfilter(g, r.img, nrm, st); })) != cudaSuccess)
+                   [&] { return launch_boxfilter(g, r.img, center, nrm, st); })) != cudaSuccess)
         return cuda_fail(e, "box filter launch");
     TcArgs a{};
     a.plane0 = p0;

@@ -43,14 +43,21 @@ size_t pool_bytes(const Geom& g);        // float32 candidate pool
 
 // ---- kernels (each launcher returns cudaGetLastError()) ----
 
-// (a1) box filter of the squared image: nrm[y][x] = sum_{u,v<p, c<C} X[y+u][x+v][c]^2
-//      int32 (uint8, exact) or float32 (float32, compensated summation).
-cudaError_t launch_boxfilter(const Geom& g, const void* img, void* nrm, cudaStream_t st);
+// Centring offset c of the operands (distances are shift-invariant):
+// uint8 -> 128 (constant, nothing written but a zero), float32 -> a sampled
+// image mean written to *center.
+cudaError_t launch_center(const Geom& g, const void* img, float* center, cudaStream_t st);
 
-// bf16 operand planes: uint8 -> one exact plane; float32 -> hi and lo planes
-// with x ~= hi + lo (hi = RN_bf16(x), lo = RN_bf16(x - hi)).
-cudaError_t launch_planes(const Geom& g, const void* img, uint16_t* plane0, uint16_t* plane1,
-                          cudaStream_t st);
+// (a1) box filter of the squared centred image:
+//      nrm[y][x] = sum_{u,v<p, c<C} (X[y+u][x+v][c] - c0)^2
+//      int32 (uint8, exact) or float32 (float32, compensated summation).
+cudaError_t launch_boxfilter(const Geom& g, const void* img, const float* center, void* nrm,
+                             cudaStream_t st);
+
+// bf16 operand planes of the centred image: uint8 -> one exact plane;
+// float32 -> hi and lo planes with x - c0 ~= hi + lo (hi = RN_bf16, lo = RN_bf16(rest)).
+cudaError_t launch_planes(const Geom& g, const void* img, const float* center, uint16_t* plane0,
+                          uint16_t* plane1, cudaStream_t st);
 
 // Plain FP32 CUDA-core direct-distance block matcher (comparison baseline).
 cudaError_t launch_direct(const Geom& g, const void* img, int32_t* out_idx, void* out_dist,

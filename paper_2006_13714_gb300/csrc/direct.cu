@@ -37,7 +37,6 @@ struct ThreadHeap {
         K = k;
         for (int i = 0; i < K; ++i) h[i * nthr] = kEmptyKey;
     }
-    __device__ __forceinline__ unsigned long long top() const { return h[0]; }
     __device__ void replace_top(unsigned long long key) {
         int i = 0;
         while (true) {
@@ -87,6 +86,44 @@ struct ThreadHeap {
     }
 };
 
+// Per-thread append buffer in front of the heap: keys below the current
+// threshold are appended with predicated stores; when any lane of the warp
+// nears a full buffer, the whole warp merges in lock-step (no divergent
+// heap work per candidate).  Loops around it are warp-uniform.
+constexpr int kBufD = 64;
+
+struct BufferedTopK {
+    ThreadHeap heap;
+    unsigned long long* buf;  // element i at buf[i * nthr]
+    int nthr, cnt;
+    unsigned long long thr;
+    __device__ void init(unsigned long long* heap_base, unsigned long long* buf_base, int t,
+                         int nthreads, int K) {
+        heap.init(heap_base, t, nthreads, K);
+        buf = buf_base + t;
+        nthr = nthreads;
+        cnt = 0;
+        thr = kEmptyKey;
+    }
+    __device__ __forceinline__ void append(unsigned long long key, bool valid) {
+        if (valid && key < thr) {
+            buf[cnt * nthr] = key;
+            ++cnt;
+        }
+    }
+    // warp-uniform call
+    __device__ void merge() {
+        const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        for (int j = 0; j < m; ++j)
+            if (j < cnt) heap.push(buf[j * nthr]);
+        cnt = 0;
+        thr = heap.h[0];
+    }
+    __device__ __forceinline__ void make_room(int need) {
+        if (__any_sync(0xffffffffu, cnt > kBufD - need)) merge();
+    }
+};
+
 struct DirectParams {
     const void* img;
     int H, W, C, p, h, s, K, n_ry, n_rx, TRy;
@@ -127,17 +164,19 @@ direct_tpl_kernel(DirectParams P) {
     float* tile = reinterpret_cast<float*>(smem);
     size_t tile_bytes = ((size_t)TY * TX * CC * 4 + 15) & ~size_t(15);
     unsigned long long* heaps = reinterpret_cast<unsigned long long*>(smem + tile_bytes);
+    unsigned long long* bufs = heaps + (size_t)blockDim.x * P.K;
     stage_tile<kU8>(P, tile, Yl, Xl, TY, TX);
-    ThreadHeap heap;
-    heap.init(heaps, threadIdx.x, blockDim.x, P.K);
+    BufferedTopK top;
+    top.init(heaps, bufs, threadIdx.x, blockDim.x, P.K);
     __syncthreads();
 
     const int ry = ry0 + threadIdx.x / 32, rx = rx0 + threadIdx.x % 32;
-    if (ry >= P.n_ry || rx >= P.n_rx) return;
+    if (ry >= P.n_ry) return;  // whole warp (one reference row per warp)
+    const bool lane_ok = rx < P.n_rx;
     const int yr = ry * P.s, xr = rx * P.s;
     const int Hc = P.H - PP + 1, Wc = P.W - PP + 1;
     const int rowf = TX * CC;
-    const int ylo = max(0, yr - h), yhi = min(Hc - 1, yr + h);
+    const int ylo = max(0, yr - h), yhi = min(Hc - 1, yr + h);  // warp-uniform
     for (int y = ylo; y <= yhi; ++y) {
         float acc[NX];
 #pragma unroll
@@ -162,16 +201,19 @@ direct_tpl_kernel(DirectParams P) {
                 }
             }
         }
+        top.make_room(NX);
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
-            int x = xr - h + i;
-            if (x >= 0 && x < Wc) heap.push(make_key(acc[i], y * P.W + x));
+            const int x = xr - h + i;
+            top.append(make_key(acc[i], y * P.W + x), lane_ok && x >= 0 && x < Wc);
         }
     }
+    top.merge();
+    if (!lane_ok) return;
     size_t ref = (size_t)ry * P.n_rx + rx;
-    heap.emit(kU8, P.out_idx + ref * P.K,
-              kU8 ? (void*)(static_cast<int32_t*>(P.out_dist) + ref * P.K)
-                  : (void*)(static_cast<float*>(P.out_dist) + ref * P.K));
+    top.heap.emit(kU8, P.out_idx + ref * P.K,
+                  kU8 ? (void*)(static_cast<int32_t*>(P.out_dist) + ref * P.K)
+                      : (void*)(static_cast<float*>(P.out_dist) + ref * P.K));
 }
 
 // Generic kernel: runtime patch / channels / window, one candidate at a time.
@@ -190,45 +232,53 @@ direct_generic_kernel(DirectParams P) {
     float* tile = reinterpret_cast<float*>(smem);
     size_t tile_bytes = kTile ? (((size_t)TY * TX * C * 4 + 15) & ~size_t(15)) : 0;
     unsigned long long* heaps = reinterpret_cast<unsigned long long*>(smem + tile_bytes);
+    unsigned long long* bufs = heaps + (size_t)blockDim.x * P.K;
     if (kTile) stage_tile<kU8>(P, tile, Yl, Xl, TY, TX);
-    ThreadHeap heap;
-    heap.init(heaps, threadIdx.x, blockDim.x, P.K);
+    BufferedTopK top;
+    top.init(heaps, bufs, threadIdx.x, blockDim.x, P.K);
     __syncthreads();
     const int ry = ry0 + threadIdx.x / 32, rx = rx0 + threadIdx.x % 32;
-    if (ry >= P.n_ry || rx >= P.n_rx) return;
+    if (ry >= P.n_ry) return;  // whole warp
+    const bool lane_ok = rx < P.n_rx;
     const int yr = ry * P.s, xr = rx * P.s;
     const int Hc = P.H - pp + 1, Wc = P.W - pp + 1;
-    const int ylo = max(0, yr - h), yhi = min(Hc - 1, yr + h);
-    const int xlo = max(0, xr - h), xhi = min(Wc - 1, xr + h);
+    const int ylo = max(0, yr - h), yhi = min(Hc - 1, yr + h);  // warp-uniform
     const int rowf = TX * C;
     for (int y = ylo; y <= yhi; ++y) {
-        for (int x = xlo; x <= xhi; ++x) {
+        for (int dx = -h; dx <= h; ++dx) {  // warp-uniform
+            const int x = xr + dx;
+            const bool ok = lane_ok && x >= 0 && x < Wc;
             float acc = 0.f;
-            for (int u = 0; u < pp; ++u) {
-                for (int e = 0; e < pp * C; ++e) {
-                    float a, b;
-                    if (kTile) {
-                        a = tile[(size_t)(yr - Yl + u) * rowf + (xr - Xl) * C + e];
-                        b = tile[(size_t)(y - Yl + u) * rowf + (x - Xl) * C + e];
-                    } else {
-                        size_t ia = ((size_t)(yr + u) * P.W + xr) * C + e;
-                        size_t ib = ((size_t)(y + u) * P.W + x) * C + e;
-                        a = kU8 ? (float)__ldg(static_cast<const uint8_t*>(P.img) + ia)
-                                : __ldg(static_cast<const float*>(P.img) + ia);
-                        b = kU8 ? (float)__ldg(static_cast<const uint8_t*>(P.img) + ib)
-                                : __ldg(static_cast<const float*>(P.img) + ib);
+            if (ok) {
+                for (int u = 0; u < pp; ++u) {
+                    for (int e = 0; e < pp * C; ++e) {
+                        float a, b;
+                        if (kTile) {
+                            a = tile[(size_t)(yr - Yl + u) * rowf + (xr - Xl) * C + e];
+                            b = tile[(size_t)(y - Yl + u) * rowf + (x - Xl) * C + e];
+                        } else {
+                            size_t ia = ((size_t)(yr + u) * P.W + xr) * C + e;
+                            size_t ib = ((size_t)(y + u) * P.W + x) * C + e;
+                            a = kU8 ? (float)__ldg(static_cast<const uint8_t*>(P.img) + ia)
+                                    : __ldg(static_cast<const float*>(P.img) + ia);
+                            b = kU8 ? (float)__ldg(static_cast<const uint8_t*>(P.img) + ib)
+                                    : __ldg(static_cast<const float*>(P.img) + ib);
+                        }
+                        float d = a - b;
+                        acc = fmaf(d, d, acc);
                     }
-                    float d = a - b;
-                    acc = fmaf(d, d, acc);
                 }
             }
-            heap.push(make_key(acc, y * P.W + x));
+            top.make_room(1);
+            top.append(make_key(acc, y * P.W + x), ok);
         }
     }
+    top.merge();
+    if (!lane_ok) return;
     size_t ref = (size_t)ry * P.n_rx + rx;
-    heap.emit(kU8, P.out_idx + ref * P.K,
-              kU8 ? (void*)(static_cast<int32_t*>(P.out_dist) + ref * P.K)
-                  : (void*)(static_cast<float*>(P.out_dist) + ref * P.K));
+    top.heap.emit(kU8, P.out_idx + ref * P.K,
+                  kU8 ? (void*)(static_cast<int32_t*>(P.out_dist) + ref * P.K)
+                      : (void*)(static_cast<float*>(P.out_dist) + ref * P.K));
 }
 
 size_t direct_smem(const Geom& g, int TRy, bool tile) {
@@ -236,7 +286,7 @@ size_t direct_smem(const Geom& g, int TRy, bool tile) {
     int TY = (TRy - 1) * g.s + NX + g.p - 1;
     int TX = 31 * g.s + NX + g.p - 1;
     size_t tb = tile ? (((size_t)TY * TX * g.C * 4 + 15) & ~size_t(15)) : 0;
-    return tb + (size_t)TRy * 32 * g.K * 8;
+    return tb + (size_t)TRy * 32 * (g.K + kBufD) * 8;
 }
 
 template <int PP, int CC, int NX>

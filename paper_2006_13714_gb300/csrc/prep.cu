@@ -13,6 +13,11 @@ namespace bm {
 namespace {
 
 constexpr int kBoxThreads = 128;
+// Distances are shift-invariant, so the operands are centred before the
+// split: uint8 by the exact constant 128, float32 by a sampled image mean.
+// Smaller magnitudes shrink ||X_r||^2 + ||X_j||^2, which bounds the error of
+// the split-precision cross term.
+constexpr int kCenterU8 = 128;
 constexpr int kBoxRows = 32;  // output rows per block (strip)
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -39,7 +44,7 @@ struct Acc2 {
 template <bool kU8>
 __global__ void __launch_bounds__(kBoxThreads)
 boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int Wc,
-                 void* __restrict__ nrm) {
+                 const float* __restrict__ center, void* __restrict__ nrm) {
     extern __shared__ unsigned char smem_raw[];
     const int x = blockIdx.x * kBoxThreads + threadIdx.x;
     if (x >= Wc) return;
@@ -53,7 +58,7 @@ boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int 
             const uint8_t* row = im + (size_t)y * row_elems + (size_t)x * C;
             int rs = 0;
             for (int e = 0; e < p * C; ++e) {
-                int v = row[e];
+                int v = (int)row[e] - kCenterU8;
                 rs += v * v;
             }
             ring[(y % p) * kBoxThreads + threadIdx.x] = rs;
@@ -67,11 +72,12 @@ boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int 
     } else {
         float2* ring = reinterpret_cast<float2*>(smem_raw);
         const float* im = static_cast<const float*>(img);
+        const float c0 = *center;
         for (int y = y0; y < y1 + p - 1; ++y) {
             const float* row = im + (size_t)y * row_elems + (size_t)x * C;
             Acc2 a{0.f, 0.f};
             for (int e = 0; e < p * C; ++e) {
-                float v = row[e];
+                float v = row[e] - c0;
                 float sq = v * v;
                 float err = fmaf(v, v, -sq);  // exact square = sq + err
                 a.add(sq);
@@ -96,8 +102,9 @@ boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int 
 // padding), then zero columns up to the pitch; rows >= H are zero.
 template <bool kU8>
 __global__ void planes_kernel(const void* __restrict__ img, int H, int W, int C, int Cp,
-                              int pitch, int rows, uint16_t* __restrict__ p0,
-                              uint16_t* __restrict__ p1) {
+                              int pitch, int rows, const float* __restrict__ center,
+                              uint16_t* __restrict__ p0, uint16_t* __restrict__ p1) {
+    const float c0 = kU8 ? (float)kCenterU8 : *center;
     const int vec_per_row = pitch / 8;
     const size_t total = (size_t)rows * vec_per_row;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
@@ -112,8 +119,8 @@ __global__ void planes_kernel(const void* __restrict__ img, int H, int W, int C,
             float v = 0.f;
             if (y < H && x < W && c < C) {
                 size_t src = ((size_t)y * W + x) * C + c;
-                v = kU8 ? (float)static_cast<const uint8_t*>(img)[src]
-                        : static_cast<const float*>(img)[src];
+                v = (kU8 ? (float)static_cast<const uint8_t*>(img)[src]
+                         : static_cast<const float*>(img)[src]) - c0;
             }
             __nv_bfloat16 h = __float2bfloat16_rn(v);
             hi[i] = __bfloat16_as_ushort(h);
@@ -135,32 +142,72 @@ __global__ void planes_kernel(const void* __restrict__ img, int H, int W, int C,
     }
 }
 
+// Sampled mean of a float32 image (one block, fixed summation order, so the
+// value is deterministic; compensated FP32 sums -- FP64 is slow on this
+// part); uint8 uses the constant 128.
+__global__ void __launch_bounds__(256) center_kernel(const float* __restrict__ img, size_t n,
+                                                     float* __restrict__ center) {
+    __shared__ float2 part[256];
+    __shared__ unsigned cnts[256];
+    const size_t step = n > (1u << 14) ? n >> 14 : 1;
+    Acc2 acc{0.f, 0.f};
+    unsigned cnt = 0;
+    for (size_t i = threadIdx.x * step; i < n; i += 256 * step) {
+        acc.add(img[i]);
+        ++cnt;
+    }
+    part[threadIdx.x] = make_float2(acc.hi, acc.lo);
+    cnts[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Acc2 s{0.f, 0.f};
+        unsigned c = 0;
+        for (int t = 0; t < 256; ++t) {
+            s.add(part[t].x);
+            s.lo += part[t].y;
+            c += cnts[t];
+        }
+        *center = c ? (s.hi + s.lo) / (float)c : 0.f;
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_boxfilter(const Geom& g, const void* img, void* nrm, cudaStream_t st) {
+cudaError_t launch_center(const Geom& g, const void* img, float* center, cudaStream_t st) {
+    if (g.dtype == kU8) {
+        // constant; nothing to compute
+        return cudaMemsetAsync(center, 0, sizeof(float), st);
+    }
+    center_kernel<<<1, 256, 0, st>>>(static_cast<const float*>(img), (size_t)g.H * g.W * g.C,
+                                     center);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boxfilter(const Geom& g, const void* img, const float* center, void* nrm,
+                             cudaStream_t st) {
     dim3 grid((g.Wc + kBoxThreads - 1) / kBoxThreads, (g.Hc + kBoxRows - 1) / kBoxRows);
     if (g.dtype == kU8) {
         size_t sm = (size_t)g.p * kBoxThreads * sizeof(int);
-        boxfilter_kernel<true><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, nrm);
+        boxfilter_kernel<true><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm);
     } else {
         size_t sm = (size_t)g.p * kBoxThreads * sizeof(float2);
-        boxfilter_kernel<false><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, nrm);
+        boxfilter_kernel<false><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_planes(const Geom& g, const void* img, uint16_t* plane0, uint16_t* plane1,
-                          cudaStream_t st) {
+cudaError_t launch_planes(const Geom& g, const void* img, const float* center, uint16_t* plane0,
+                          uint16_t* plane1, cudaStream_t st) {
     size_t total = (size_t)g.plane_rows * (g.plane_pitch / 8);
     int threads = 256;
     int blocks = (int)((total + threads - 1) / threads);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (g.dtype == kU8)
         planes_kernel<true><<<blocks, threads, 0, st>>>(img, g.H, g.W, g.C, g.Cp, g.plane_pitch,
-                                                        g.plane_rows, plane0, plane1);
+                                                        g.plane_rows, center, plane0, plane1);
     else
         planes_kernel<false><<<blocks, threads, 0, st>>>(img, g.H, g.W, g.C, g.Cp, g.plane_pitch,
-                                                         g.plane_rows, plane0, plane1);
+                                                         g.plane_rows, center, plane0, plane1);
     return cudaGetLastError();
 }
 

@@ -91,11 +91,11 @@ __device__ __forceinline__ int pick(const int (&a)[N], int i) {
 
 // Rank of every member (lane-strided slots) by (key, off) ascending.
 template <int N>
-__device__ void rank_members(const double (&key)[N], const int (&off)[N], int nb, int lane,
+__device__ void rank_members(const double (&key)[N], const int (&off)[N], int nslots, int lane,
                              int (&rank)[N]) {
 #pragma unroll
     for (int i = 0; i < N; ++i) rank[i] = 0;
-    for (int m = 0; m < nb; ++m) {
+    for (int m = 0; m < nslots; ++m) {
         const int src = m & 31, slot = m >> 5;
         const double km = __shfl_sync(0xffffffffu, pick(key, slot), src);
         const int om = __shfl_sync(0xffffffffu, pick(off, slot), src);
@@ -107,19 +107,21 @@ __device__ void rank_members(const double (&key)[N], const int (&off)[N], int nb
     }
 }
 
-// Final selection over nb members (distances d32 in key[], offsets in off[]):
+// Final selection over the first nslots lane-strided slots, nb of which are
+// members (non-members carry key +inf and rank after every member):
 // FP64 refinement at the K-th boundary, then write ranks < K.
 template <int N>
 __device__ void select_and_write(const RerankParams& P, const float* ref, double (&key)[N],
-                                 int (&off)[N], int nb, int lane, size_t r, float gamma) {
+                                 int (&off)[N], int nslots, int nb, int lane, size_t r,
+                                 float gamma) {
     int rank[N];
-    rank_members(key, off, nb, lane, rank);
+    rank_members(key, off, nslots, lane, rank);
     if (nb > P.K) {
         // distances at ranks K-1 (last in) and K (first out), broadcast to the warp
         double din = 0.0, dout = 0.0;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const bool m = lane + 32 * i < nb;
+            const bool m = lane + 32 * i < nslots;
             din += (m && rank[i] == P.K - 1) ? key[i] : 0.0;
             dout += (m && rank[i] == P.K) ? key[i] : 0.0;
         }
@@ -133,20 +135,21 @@ __device__ void select_and_write(const RerankParams& P, const float* ref, double
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 const int m = lane + 32 * i;
-                if (m < nb && key[i] >= din - 2.0 * tol && key[i] <= dout + 2.0 * tol) {
+                if (m < nslots && rank[i] < nb && key[i] >= din - 2.0 * tol &&
+                    key[i] <= dout + 2.0 * tol) {
                     key[i] = direct_f64(P, ref, off[i] / P.W, off[i] % P.W);
                     ++nrec;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
             if (lane == 0 && nrec) atomicAdd(P.counters + 1, (unsigned long long)nrec);
-            rank_members(key, off, nb, lane, rank);
+            rank_members(key, off, nslots, lane, rank);
         }
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const int m = lane + 32 * i;
-        if (m < nb && rank[i] < P.K) {
+        if (m < nslots && rank[i] < nb && rank[i] < P.K) {
             P.out_idx[r * P.K + rank[i]] = off[i];
             P.out_dist[r * P.K + rank[i]] = (float)key[i];
         }
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     const float nr = P.nrm[(size_t)yr * P.Wc + xr];
     const float gamma = (float)(pc * P.p + 3) * 5.9604645e-08f;  // (n + 3) 2^-24
 
-    // ---- load the pool (sorted by v descending; empties last)
+    // ---- load the pool (any order; empty slots have offset -1)
     float v[kSlots];
     int off[kSlots];
     float nc[kSlots];
@@ -197,25 +200,46 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     }
     for (int o = 16; o > 0; o >>= 1) npool += __shfl_xor_sync(0xffffffffu, npool, o);
 
-    // ---- band: prefix of the pool with v >= T'
+    // ---- band: entries with v >= T' (see the file header)
+    bool member[kSlots];
+#pragma unroll
+    for (int i = 0; i < kSlots; ++i) member[i] = off[i] >= 0;
     int nb = npool;
     bool overflow = false;
     if (npool > P.K) {
-        float ncmax = 0.f;
+        // rank of every entry by v descending (ties: slot order)
+        int rk[kSlots];
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i)
-            if (lane + 32 * i < P.K) ncmax = fmaxf(ncmax, nc[i]);
-        for (int o = 16; o > 0; o >>= 1) ncmax = fmaxf(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
-        const int kk = P.K - 1;
-        float vK = 0.f;
+        for (int i = 0; i < kSlots; ++i) rk[i] = 0;
+        for (int m = 0; m < P.L; ++m) {
+            const int src = m & 31, slot = m >> 5;
+            float vm = v[0];
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) vK = (kk >> 5) == i ? v[i] : vK;
-        vK = __shfl_sync(0xffffffffu, vK, kk & 31);
+            for (int k = 1; k < kSlots; ++k) vm = slot == k ? v[k] : vm;
+            vm = __shfl_sync(0xffffffffu, vm, src);
+#pragma unroll
+            for (int i = 0; i < kSlots; ++i) {
+                const int me = lane + 32 * i;
+                rk[i] += (vm > v[i] || (vm == v[i] && m < me)) ? 1 : 0;
+            }
+        }
+        float vK = -__int_as_float(0x7f800000), ncmax = 0.f;
+#pragma unroll
+        for (int i = 0; i < kSlots; ++i) {
+            if (off[i] >= 0 && rk[i] == P.K - 1) vK = v[i];
+            if (off[i] >= 0 && rk[i] < P.K) ncmax = fmaxf(ncmax, nc[i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            vK = fmaxf(vK, __shfl_xor_sync(0xffffffffu, vK, o));
+            ncmax = fmaxf(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
+        }
         const float tb = vK - 2.0f * kEps * (nr + ncmax) * 1.0001f;
         int cnt = 0;
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i)
-            if (lane + 32 * i < npool && v[i] >= tb) ++cnt;
+        for (int i = 0; i < kSlots; ++i) {
+            member[i] = off[i] >= 0 && v[i] >= tb;
+            cnt += member[i] ? 1 : 0;
+        }
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         nb = cnt;
         overflow = (npool == P.L) && (nb == P.L);
@@ -226,18 +250,20 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         int viol = 0;
 #pragma unroll
         for (int i = 0; i < kSlots; ++i) {
-            key[i] = 0.0;
-            if (lane + 32 * i < nb) {
+            key[i] = __longlong_as_double(0x7ff0000000000000ll);  // +inf: not a member
+            if (member[i]) {
                 const float d32 = direct_f32(P, ref, off[i] / P.W, off[i] % P.W);
                 key[i] = d32;
                 // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
                 const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
                 if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f) ++viol;
+            } else {
+                off[i] = 0x7fffffff;
             }
         }
         for (int o = 16; o > 0; o >>= 1) viol += __shfl_xor_sync(0xffffffffu, viol, o);
         if (lane == 0 && viol) atomicAdd(P.counters + 2, (unsigned long long)viol);
-        select_and_write(P, ref, key, off, nb, lane, r, gamma);
+        select_and_write(P, ref, key, off, P.L, nb, lane, r, gamma);
         return;
     }
 
@@ -294,7 +320,7 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         cnt += (k != ~0ull) ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    select_and_write(P, ref, key2, off2, cnt, lane, r, gamma);
+    select_and_write(P, ref, key2, off2, cnt, cnt, lane, r, gamma);
 }
 
 }  // namespace

@@ -59,14 +59,16 @@ constexpr float kEps = 6.103515625e-05f;  // 2^-14
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kSmemLimit = 227 * 1024;
+constexpr int kBuf = 32;  // per-lane append buffer (entries) between heap merges
 
 struct TcGeom {
     int H, W, Cp, p, h, s, K, HL, n_ry, n_rx, Hc, Wc;
+    int rr, rc, wgx, ty, tx;  // lane -> reference mapping and tile shape (references)
     int pw, p_eff, nkc, Rb, kcols;
     int qpitch, plane_stage, ns_bytes, stage_bytes;
     int plane_pitch;
     int f32;
-    int off_a0, off_a1, off_an, off_stage, off_heap, off_bar, smem_total;
+    int off_a0, off_a1, off_an, off_stage, off_heap, off_buf, off_bar, smem_total;
 };
 
 struct TcParams {
@@ -107,12 +109,25 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait with a suspend-time hint (ns): the waiting thread sleeps until the
+// phase completes or the hint elapses instead of spinning on the barrier.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(1000000u)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait on one mbarrier phase.  False on timeout or abort.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int code) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity)) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitNs) {
             *abort_flag = code;
@@ -153,20 +168,48 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
         : "memory");
 }
-// 32 lanes x 16 consecutive columns, waited before returning.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+// 32 lanes x (16 * NB) columns: NB aligned x16 loads at taddr + 16*b, one wait.
+template <int NB>
+__device__ __forceinline__ void tmem_ld_blocks(uint32_t taddr, float* v);
+template <>
+__device__ __forceinline__ void tmem_ld_blocks<1>(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
         "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + 0u)
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_blocks<2>(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 0u), "r"(taddr + 16u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_blocks<4>(uint32_t taddr, float* v) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%67];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ float max3(float a, float b, float c) {
     float m;
@@ -230,7 +273,9 @@ __device__ __forceinline__ uint4 load_shifted16(const uint16_t* row, int e0) {
     return o;
 }
 
-// Max-heap of u64 keys per epilogue thread, element i at h[i * 128].
+// 4-ary max-heap of u64 keys per epilogue thread, element i at h[i * 128]
+// (the four children of a node are loaded together: half the dependent
+// shared-memory round trips of a binary heap).
 struct Heap {
     unsigned long long* h;
     int n;
@@ -238,14 +283,15 @@ struct Heap {
     __device__ void replace_top(unsigned long long key) {
         int i = 0;
         while (true) {
-            int l = 2 * i + 1;
-            if (l >= n) break;
-            int r = l + 1;
-            unsigned long long cv = h[l * 128];
-            int c = l;
-            if (r < n) {
-                unsigned long long rv = h[r * 128];
-                if (rv > cv) { cv = rv; c = r; }
+            const int c0 = 4 * i + 1;
+            if (c0 >= n) break;
+            unsigned long long cv = h[c0 * 128];
+            int c = c0;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                const int ck = c0 + k;
+                const unsigned long long v = ck < n ? h[ck * 128] : 0ull;
+                if (v > cv) { cv = v; c = ck; }
             }
             if (cv <= key) break;
             h[i * 128] = cv;
@@ -267,18 +313,116 @@ struct Heap {
     }
 };
 
+// Register-resident sorted list of the best keys (ascending), capacity LC,
+// of which the first `cap` entries are used.  insert() is a branch-free
+// insertion network: a key that is not better than entry cap-1 changes
+// nothing, so every lane of a warp can run it in lock-step.
+template <int LC>
+struct RegTopK {
+    unsigned long long a[LC];
+    int cap;
+    __device__ __forceinline__ void init(int c) {
+        cap = c;
+#pragma unroll
+        for (int i = 0; i < LC; ++i) a[i] = kEmpty;
+    }
+    __device__ __forceinline__ void insert(unsigned long long k) {
+        bool lt[LC];
+#pragma unroll
+        for (int i = 0; i < LC; ++i) lt[i] = k < a[i];
+#pragma unroll
+        for (int i = LC - 1; i > 0; --i)
+            if (i < cap) a[i] = lt[i - 1] ? a[i - 1] : (lt[i] ? k : a[i]);
+        a[0] = lt[0] ? k : a[0];
+    }
+    __device__ __forceinline__ unsigned long long kth() const {  // entry cap-1 (the largest used)
+        unsigned long long r = 0;
+#pragma unroll
+        for (int i = 0; i < LC; ++i) {
+            const unsigned long long x = i < cap ? a[i] : 0ull;
+            r = x > r ? x : r;
+        }
+        return r;
+    }
+};
+
+// Warp-synchronous merge of every lane's pending entries (call from all 32
+// lanes): one pending entry per lane per step goes through the selection.
+template <int LC>
+__device__ __forceinline__ void merge_pending(const TcGeom& G, const int* nrm_i, int nr_i,
+                                              unsigned long long* pend, int& cnt, float& thr,
+                                              RegTopK<LC == 0 ? 1 : LC>& reg, Heap& heap) {
+    const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    for (int j0 = 0; j0 < m; j0 += 4) {
+        unsigned long long e[4];
+        int par[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = j0 + t;
+            e[t] = j < cnt ? pend[j * 128] : kEmpty;
+            par[t] = 0;
+            if (!G.f32 && j < cnt) {
+                const unsigned off = (unsigned)(e[t] & 0xffffffffu);
+                const unsigned yc = off / (unsigned)G.W, xc = off - yc * (unsigned)G.W;
+                par[t] = nrm_i[(size_t)yc * G.Wc + xc] & 1;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            unsigned long long key = kEmpty;
+            if (e[t] != kEmpty) {
+                const float v = __uint_as_float((unsigned)(e[t] >> 32));
+                const unsigned long long off = e[t] & 0xffffffffull;
+                if (G.f32) {
+                    key = ((unsigned long long)(~orderable(v)) << 32) | off;
+                } else {
+                    const int dd = nr_i - 2 * (int)v + par[t];
+                    key = ((unsigned long long)(unsigned)dd << 32) | off;
+                }
+            }
+            if (LC > 0) {
+                reg.insert(key);
+            } else if (key < heap.top()) {
+                heap.replace_top(key);
+            }
+        }
+    }
+    cnt = 0;
+    const unsigned long long t = LC > 0 ? reg.kth() : heap.top();
+    if (t != kEmpty) {
+        if (G.f32) thr = from_orderable(~(unsigned)(t >> 32));
+        else thr = (float)((nr_i - (int)(t >> 32)) >> 1) - 1.0f;
+    }
+}
+
+// Chunk visiting order: centre-first.  Chunk 0 holds the candidate columns
+// at the tile's centre, then alternately right and left, so every reference
+// sees its nearest (usually best) candidates first and its threshold
+// tightens early.
+__device__ __forceinline__ int chunk_order(int c, int n, int cc) {
+    const int left = cc, right = n - 1 - cc, m = min(left, right);
+    if (c <= 2 * m) {
+        const int k = (c + 1) >> 1;
+        return (c & 1) ? cc + k : cc - k;
+    }
+    const int rest = c - 2 * m;
+    return left > right ? cc - m - rest : cc + m + rest;
+}
+
 // ---------------------------------------------------------------- the kernel
+template <int LC>  // register list capacity (16, 32), or 0 for the shared-memory heap
 __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcGeom& G = P.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int ry0 = blockIdx.y * 4, rx0 = blockIdx.x * 32;
-    const int ry_last = min(ry0 + 3, G.n_ry - 1), rx_last = min(rx0 + 31, G.n_rx - 1);
+    const int ry0 = blockIdx.y * G.ty, rx0 = blockIdx.x * G.tx;
+    const int ry_last = min(ry0 + G.ty - 1, G.n_ry - 1), rx_last = min(rx0 + G.tx - 1, G.n_rx - 1);
     const int Y0 = max(0, ry0 * G.s - G.h), Y1 = min(G.Hc - 1, ry_last * G.s + G.h);
     const int X0 = max(0, rx0 * G.s - G.h), X1 = min(G.Wc - 1, rx_last * G.s + G.h);
     const int NR = Y1 - Y0 + 1, NX = X1 - X0 + 1;
     const int nchunks = (NX + G.kcols - 1) / G.kcols;
+    const int center_chunk = min(nchunks - 1, ((rx0 + rx_last) * G.s / 2 - X0) / G.kcols);
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G.off_bar);
     const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kStages);
@@ -311,7 +455,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             const int pl = t / items, it = t % items;
             const int m = it / G.nkc, kc = it % G.nkc;
             const int u = kc / G.pw, q = kc % G.pw;
-            const int ry = ry0 + (m >> 5), rx = rx0 + (m & 31);
+            const int mw = m >> 5, ml = m & 31;
+            const int ry = ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
+            const int rx = rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (ry < G.n_ry && rx < G.n_rx && u < G.p) {
                 const uint16_t* plane = pl ? P.plane1 : P.plane0;
@@ -373,23 +519,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             const int stage = c % kStages, use = c / kStages;
             if (use > 0 && !mbar_wait(bar_empty + 8 * stage, (use - 1) & 1, abort_flag, 1)) break;
             uint8_t* sb = smem + G.off_stage + stage * G.stage_bytes;
-            const int jc0 = c * G.kcols;
+            const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
             const int kc_here = min(G.kcols, NX - jc0);
-            for (int t = pt; t < strip_items; t += 128) {
-                int r = t;
-                const int row = r % G.Rb; r /= G.Rb;
-                const int jl = r % G.kcols; r /= G.kcols;
-                const int q = r % G.pw;
-                const int pl = r / G.pw;
-                if (jl >= kc_here) continue;
-                uint4 val = make_uint4(0, 0, 0, 0);
-                if (row < NR + G.p_eff - 1) {  // rows past that feed no real candidate
-                    const uint16_t* plane = pl ? P.plane1 : P.plane0;
-                    const uint16_t* prow = plane + (size_t)(Y0 + row) * G.plane_pitch;
-                    val = load_shifted16(prow, (X0 + jc0 + jl) * G.Cp + 8 * q);
+            for (int t0 = pt; t0 < strip_items; t0 += 4 * 128) {
+                uint4 val[4];
+                int dst[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int t = t0 + k * 128;
+                    dst[k] = -1;
+                    val[k] = make_uint4(0, 0, 0, 0);
+                    if (t >= strip_items) continue;
+                    int r = t;
+                    const int row = r % G.Rb; r /= G.Rb;
+                    const int jl = r % G.kcols; r /= G.kcols;
+                    const int q = r % G.pw;
+                    const int pl = r / G.pw;
+                    if (jl >= kc_here) continue;
+                    dst[k] = pl * G.plane_stage + q * G.qpitch + (jl * G.Rb + row) * 16;
+                    if (row < NR + G.p_eff - 1) {  // rows past that feed no real candidate
+                        const uint16_t* plane = pl ? P.plane1 : P.plane0;
+                        const uint16_t* prow = plane + (size_t)(Y0 + row) * G.plane_pitch;
+                        val[k] = load_shifted16(prow, (X0 + jc0 + jl) * G.Cp + 8 * q);
+                    }
                 }
-                *reinterpret_cast<uint4*>(sb + pl * G.plane_stage + q * G.qpitch +
-                                          (jl * G.Rb + row) * 16) = val;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (dst[k] >= 0) *reinterpret_cast<uint4*>(sb + dst[k]) = val[k];
             }
             uint8_t* nsb = sb + nplanes * G.plane_stage;
             for (int t = pt; t < norm_items; t += 128) {
@@ -430,7 +586,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                 if (ub > 0 && !mbar_wait(bar_tempty + 8 * buf, (ub - 1) & 1, abort_flag, 2)) break;
                 if (!mbar_wait(bar_full + 8 * stage, use & 1, abort_flag, 3)) break;
                 tc_fence_after();
-                const int kc_here = min(G.kcols, NX - c * G.kcols);
+                const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
+                const int kc_here = min(G.kcols, NX - jc0);
                 const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
                 const uint32_t d = tmem_base + buf * kBufCols;
                 const uint32_t sb = smem_u32(smem + G.off_stage + stage * G.stage_bytes);
@@ -464,71 +621,75 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
+        // Per lane: a max-heap of the best keys (uint8: (d, offset), float32:
+        // (-v, offset)) and an append buffer.  Values at or above the lane's
+        // threshold are appended with predicated stores (no divergent work);
+        // when any lane's buffer nears full the whole warp merges its buffers
+        // into the heaps in lock-step.
         Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + threadIdx.x, G.HL};
-        const int ry = ry0 + warp, rx = rx0 + lane;
-        const bool row_ok = ry < G.n_ry;
-        const bool lane_ok = row_ok && rx < G.n_rx;
+        RegTopK<LC == 0 ? 1 : LC> reg;
+        reg.init(G.HL);
+        unsigned long long* pend = reinterpret_cast<unsigned long long*>(smem + G.off_buf) + threadIdx.x;
+        const int ry = ry0 + (warp / G.wgx) * G.rr + lane / G.rc;
+        const int rx = rx0 + (warp % G.wgx) * G.rc + lane % G.rc;
+        const bool lane_ok = ry < G.n_ry && rx < G.n_rx;
         const int yr = ry * G.s, xr = rx * G.s;
-        const int lo = max(0, yr - G.h - Y0), hi = min(NR - 1, yr + G.h - Y0);
-        int nr_i = 0;
+        // this lane's candidate rows inside the strip (empty if the lane has no reference)
+        const int lo = lane_ok ? max(0, yr - G.h - Y0) : 1 << 20;
+        const int hi = lane_ok ? min(NR - 1, yr + G.h - Y0) : -1;
         const int* nrm_i = static_cast<const int*>(P.nrm);
-        if (lane_ok && !G.f32) nr_i = nrm_i[(size_t)yr * G.Wc + xr];
-        float thr = -__int_as_float(0x7f800000);  // -inf while the heap has empty slots
+        const int nr_i = (lane_ok && !G.f32) ? nrm_i[(size_t)yr * G.Wc + xr] : 0;
+        float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
+        int cnt = 0;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         for (int c = 0; c < nchunks; ++c) {
             const int buf = c & 1, ub = c >> 1;
             if (!mbar_wait(bar_tfull + 8 * buf, ub & 1, abort_flag, 4)) break;
             tc_fence_after();
-            const int jc0 = c * G.kcols;
+            const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
             const int kc_here = min(G.kcols, NX - jc0);
-            if (row_ok) {
-                for (int jl = 0; jl < kc_here; ++jl) {
-                    const int xc = X0 + jc0 + jl;
-                    const bool xok = lane_ok && abs(xc - xr) <= G.h;
-                    if (!__any_sync(0xffffffffu, xok)) continue;
-                    const uint32_t colbase = tmem_base + lane_base + buf * kBufCols + jl * G.Rb;
-                    for (int b = lo >> 4; b <= (hi >> 4); ++b) {
-                        float v[16];
-                        tmem_ld16(colbase + 16 * b, v);
-                        const int i0 = max(lo - 16 * b, 0), i1 = min(hi - 16 * b, 15);
-                        float m;
-                        if (i0 == 0 && i1 == 15) {
-                            float a = max3(v[0], v[1], v[2]), bq = max3(v[3], v[4], v[5]);
-                            float cq = max3(v[6], v[7], v[8]), dq = max3(v[9], v[10], v[11]);
-                            float e = max3(v[12], v[13], v[14]);
-                            m = max3(max3(a, bq, cq), max3(dq, e, v[15]), a);
-                        } else {
-                            m = -__int_as_float(0x7f800000);
+            for (int jl = 0; jl < kc_here; ++jl) {
+                const int xc = X0 + jc0 + jl;
+                const bool xok = lane_ok && abs(xc - xr) <= G.h;
+                if (!__any_sync(0xffffffffu, xok)) continue;
+                // rows any lane of the warp needs in this column (warp-uniform)
+                const int wlo = __reduce_min_sync(0xffffffffu, xok ? lo : 1 << 20);
+                const int whi = __reduce_max_sync(0xffffffffu, xok ? hi : -1);
+                const int b0 = wlo >> 4, nblk = (whi >> 4) - b0 + 1;
+                const uint32_t colbase = tmem_base + lane_base + buf * kBufCols + jl * G.Rb + 16 * b0;
+                for (int bb = 0; bb < nblk; bb += 2) {
+                    const int nb = min(2, nblk - bb);
+                    float v[32];
+                    if (nb == 2) tmem_ld_blocks<2>(colbase + 16 * bb, v);
+                    else tmem_ld_blocks<1>(colbase + 16 * bb, v);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                if (i >= i0 && i <= i1) m = fmaxf(m, v[i]);
+                    for (int t = 0; t < 2; ++t) {
+                        if (t >= nb) break;
+                        const int b = b0 + bb + t;
+                        // this lane's valid rows of block b: [i0, i1] (may be empty)
+                        const int i0 = lo - 16 * b, i1 = xok ? hi - 16 * b : -1;
+                        const float* w = v + 16 * t;
+                        const float ninf = -__int_as_float(0x7f800000);
+                        float m = ninf;
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const float a = (i >= i0 && i <= i1) ? w[i] : ninf;
+                            const float c2 = (i + 1 >= i0 && i + 1 <= i1) ? w[i + 1] : ninf;
+                            m = max3(m, a, c2);
                         }
-                        if (xok && m >= thr) {
-                            // slow path: exact keys for every candidate at or above the threshold
+                        const bool hit = m >= thr;
+                        if (!__any_sync(0xffffffffu, hit)) continue;
+                        if (__any_sync(0xffffffffu, cnt > kBuf - 16))
+                            merge_pending<LC>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+                        if (hit) {
+                            const int ybase = Y0 + 16 * b;
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                if (i < i0 || i > i1 || !(v[i] >= thr)) continue;
-                                const int yc = Y0 + 16 * b + i;
-                                const unsigned off = (unsigned)(yc * G.W + xc);
-                                unsigned long long key;
-                                if (G.f32) {
-                                    key = ((unsigned long long)(~orderable(v[i])) << 32) | off;
-                                } else {
-                                    const int nc = nrm_i[(size_t)yc * G.Wc + xc];
-                                    const int dd = nr_i - 2 * (int)v[i] + (nc & 1);
-                                    key = ((unsigned long long)(unsigned)dd << 32) | off;
-                                }
-                                if (key < heap.top()) {
-                                    heap.replace_top(key);
-                                    const unsigned long long t = heap.top();
-                                    if (t != kEmpty) {
-                                        if (G.f32) {
-                                            thr = from_orderable(~(unsigned)(t >> 32));
-                                        } else {
-                                            const int dk = (int)(t >> 32);
-                                            thr = (float)((nr_i - dk) >> 1) - 1.0f;
-                                        }
-                                    }
+                                if (i >= i0 && i <= i1 && w[i] >= thr) {
+                                    pend[cnt * 128] =
+                                        ((unsigned long long)__float_as_uint(w[i]) << 32) |
+                                        (unsigned)((ybase + i) * G.W + xc);
+                                    ++cnt;
                                 }
                             }
                         }
@@ -538,32 +699,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             tc_fence_before();
             mbar_arrive(bar_tempty + 8 * buf);
         }
+        merge_pending<LC>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
         // ---- write results
         if (lane_ok && !*abort_flag) {
-            heap.sort();
             const size_t ref = (size_t)ry * G.n_rx + rx;
-            if (G.f32) {
-                for (int k = 0; k < G.HL; ++k) {
-                    const unsigned long long key = heap.h[k * 128];
-                    if (key == kEmpty) {
-                        P.pool_idx[ref * G.HL + k] = -1;
-                        P.pool_score[ref * G.HL + k] = -__int_as_float(0x7f800000);
-                    } else {
-                        P.pool_idx[ref * G.HL + k] = (int32_t)(unsigned)(key & 0xffffffffu);
-                        P.pool_score[ref * G.HL + k] = from_orderable(~(unsigned)(key >> 32));
-                    }
+            if (LC == 0 && !G.f32) heap.sort();
+            const int nout = G.f32 ? G.HL : G.K;
+            auto emit = [&](int k, unsigned long long key) {
+                if (G.f32) {
+                    // pool: any order; the re-rank kernel ranks it
+                    P.pool_idx[ref * G.HL + k] = key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
+                    P.pool_score[ref * G.HL + k] = key == kEmpty ? -__int_as_float(0x7f800000)
+                                                                : from_orderable(~(unsigned)(key >> 32));
+                } else {
+                    P.out_idx[ref * G.K + k] = key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
+                    P.out_dist[ref * G.K + k] = key == kEmpty ? 0x7fffffff : (int32_t)(unsigned)(key >> 32);
                 }
+            };
+            if (LC > 0) {
+#pragma unroll
+                for (int i = 0; i < (LC == 0 ? 1 : LC); ++i)
+                    if (i < nout) emit(i, reg.a[i]);
             } else {
-                for (int k = 0; k < G.K; ++k) {
-                    const unsigned long long key = heap.h[k * 128];
-                    if (key == kEmpty) {
-                        P.out_idx[ref * G.K + k] = -1;
-                        P.out_dist[ref * G.K + k] = 0x7fffffff;
-                    } else {
-                        P.out_idx[ref * G.K + k] = (int32_t)(unsigned)(key & 0xffffffffu);
-                        P.out_dist[ref * G.K + k] = (int32_t)(unsigned)(key >> 32);
-                    }
-                }
+                for (int k = 0; k < nout; ++k) emit(k, heap.h[k * 128]);
             }
         }
     }
@@ -584,9 +742,25 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
     t.f32 = g.dtype == kF32;
     t.HL = t.f32 ? g.L : g.K;
     t.plane_pitch = g.plane_pitch;
-    const int nr_max = 3 * g.s + 2 * g.h + 1;
-    t.Rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
-    if (t.Rb > kBufCols) return false;
+    // lane -> reference mapping: rr reference rows x rc columns per warp, a
+    // wgy x wgx grid of 4 warps; pick the one with the least MMA work
+    // (union columns x strip rows), preferring narrow warps (rc small) on ties.
+    static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
+    long long best = -1;
+    for (const auto& mp : kMaps) {
+        const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
+        const int ty = wgy * rr, tx = wgx * rc;
+        const int nr_max = (ty - 1) * g.s + 2 * g.h + 1;
+        const int nx_max = (tx - 1) * g.s + 2 * g.h + 1;
+        const int rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
+        if (rb > kBufCols) continue;
+        const long long work = (long long)nx_max * rb;
+        if (best < 0 || work < best) {
+            best = work;
+            t.rr = rr; t.rc = rc; t.wgx = wgx; t.ty = ty; t.tx = tx; t.Rb = rb;
+        }
+    }
+    if (best < 0) return false;
     t.kcols = kBufCols / t.Rb;
     const int strip_rows = t.kcols * t.Rb + g.p_eff + 16;
     t.qpitch = strip_rows * 16;
@@ -601,6 +775,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
     t.off_an = off; off += 128 * 2 * 16;
     t.off_stage = off; off += kStages * t.stage_bytes;
     t.off_heap = off; off += 128 * t.HL * 8;
+    t.off_buf = off; off += 128 * kBuf * 8;
     t.off_bar = off; off += (2 * kStages + 5) * 8 + 16;
     t.smem_total = (off + 1023) / 1024 * 1024;
     // the plane padding covers the widest read (see make_geom)
@@ -627,9 +802,11 @@ cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {
     P.status = a.status;
     // at least 114 KB of shared memory keeps one CTA per SM (whole-TMEM allocation)
     const int smem = P.g.smem_total < 116 * 1024 ? 116 * 1024 : P.g.smem_total;
-    cudaFuncSetAttribute(tc_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    dim3 grid((g.n_rx + 31) / 32, (g.n_ry + 3) / 4);
-    tc_match_kernel<<<grid, kThreads, smem, st>>>(P);
+    dim3 grid((g.n_rx + P.g.tx - 1) / P.g.tx, (g.n_ry + P.g.ty - 1) / P.g.ty);
+    auto kern = P.g.HL <= 16 ? tc_match_kernel<16> : P.g.HL <= 32 ? tc_match_kernel<32>
+                                                                  : tc_match_kernel<0>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kern<<<grid, kThreads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
