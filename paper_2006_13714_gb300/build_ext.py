@@ -53,7 +53,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-        cmd = common + ["-c", src, "-o", obj]
+        extra = ["-maxrregcount=224"] if os.path.basename(src) == "selfconv_tc.cu" else []
+        cmd = common + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -2,26 +2,27 @@
 //
 // The tensor-core pass leaves, per reference r, a pool of the L largest
 // v_j = b~_j + eps n_j (b~ the split-bf16 estimate of Theorem 1's score
-// b_j = C_r(j) - 0.5 n_j, n_j = ||X_j||^2, eps = 2^-14) sorted by v
-// descending.  The identity d = ||X_r||^2 - 2 b (Lemma 2) loses precision to
-// cancellation in proportion to ||X_r||^2 + ||X_j||^2, not to d, so the
-// final distances are recomputed here directly:
+// b_j = C_r(j) - 0.5 n_j of the centred patches, n_j = ||X_j - c||^2,
+// eps = 2^-14), in any order.  The identity d = ||X_r||^2 - 2 b (Lemma 2)
+// loses precision to cancellation in proportion to n_r + n_j, not to d, so
+// the final distances are recomputed here directly:
 //
 //   1. Error bound: |b~_j - b_j| <= eps (n_r + n_j).  At least K pool
-//      entries have b >= T' = v_K - eps n_r - 2 eps max_{k<=K} n_k, so only
-//      entries with u_j = v_j + eps n_r >= T' can be among the K nearest:
-//      a prefix of the pool (the band).  If the pool is full and its last
-//      entry is still in the band, candidates outside the pool might be too
-//      ("overflow"): that reference is recomputed over its whole window.
+//      entries have b >= T' = v_K - eps n_r - 2 eps max_{rank<K} n_k, so only
+//      entries with u_j = v_j + eps n_r >= T' can be among the K nearest (the
+//      band).  If the pool is full and every entry is in the band,
+//      candidates outside the pool might qualify too ("overflow"): that
+//      reference is recomputed over its whole window.
 //   2. Band members get the explicit FP32 distance sum (X_r - X_j)^2
 //      (Eq. equ:bmMetric_app), relative error <= gamma = (n + 3) 2^-24 with
 //      n = p*p*C terms, and are ranked by (distance, row-major offset).
 //   3. If the K-th and (K+1)-th FP32 distances are within that error of each
-//      other, the members near the boundary are recomputed in FP64 and the
-//      order there is decided by the FP64 values.
-//   4. Debug counter: band members whose identity estimate misses the direct
-//      distance by more than the stated bound (should stay 0).
-// One warp per reference.
+//      other, the members near the boundary are recomputed in FP64 and their
+//      order there follows the FP64 values.
+//   4. Counter: band members whose identity estimate misses the direct
+//      distance by more than the bound (expected 0).
+// One warp per reference; every ranking uses 64-bit integer keys (FP64 is
+// slow on this part and is kept to the rare boundary ties).
 #include "bm_internal.h"
 
 #include <climits>
@@ -31,9 +32,8 @@ namespace {
 
 constexpr float kEps = 6.103515625e-05f;  // 2^-14, same constant as the tensor-core pass
 constexpr int kWarps = 4;
-constexpr int kMaxPool = 192;             // >= every pool length L
-constexpr int kSlots = kMaxPool / 32;     // pool entries per lane
 constexpr int kFbSlots = (kMaxK + 1 + 31) / 32;
+constexpr unsigned long long kNone = ~0ull;
 
 struct RerankParams {
     const float* img;
@@ -52,6 +52,7 @@ __device__ __forceinline__ float direct_f32(const RerankParams& P, const float* 
     for (int u = 0; u < P.p; ++u) {
         const float* crow = P.img + ((size_t)(yc + u) * P.W + xc) * P.C;
         const float* rrow = ref + u * pc;
+#pragma unroll 8
         for (int e = 0; e < pc; ++e) {
             const float d = rrow[e] - __ldg(crow + e);
             acc = fmaf(d, d, acc);
@@ -74,84 +75,108 @@ __device__ __forceinline__ double direct_f64(const RerankParams& P, const float*
     return acc;
 }
 
-template <int N>
-__device__ __forceinline__ double pick(const double (&a)[N], int i) {
-    double r = a[0];
+// rank[i] = number of keys (over all 32*S lane-strided slots) smaller than key[i].
+template <int S>
+__device__ __forceinline__ void warp_rank(const unsigned long long (&key)[S], int (&rank)[S]) {
 #pragma unroll
-    for (int k = 1; k < N; ++k) r = (i == k) ? a[k] : r;
-    return r;
-}
-template <int N>
-__device__ __forceinline__ int pick(const int (&a)[N], int i) {
-    int r = a[0];
+    for (int i = 0; i < S; ++i) rank[i] = 0;
 #pragma unroll
-    for (int k = 1; k < N; ++k) r = (i == k) ? a[k] : r;
-    return r;
-}
-
-// Rank of every member (lane-strided slots) by (key, off) ascending.
-template <int N>
-__device__ void rank_members(const double (&key)[N], const int (&off)[N], int nslots, int lane,
-                             int (&rank)[N]) {
+    for (int slot = 0; slot < S; ++slot) {
+        for (int src = 0; src < 32; ++src) {
+            const unsigned long long km = __shfl_sync(0xffffffffu, key[slot], src);
 #pragma unroll
-    for (int i = 0; i < N; ++i) rank[i] = 0;
-    for (int m = 0; m < nslots; ++m) {
-        const int src = m & 31, slot = m >> 5;
-        const double km = __shfl_sync(0xffffffffu, pick(key, slot), src);
-        const int om = __shfl_sync(0xffffffffu, pick(off, slot), src);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const bool lt = km < key[i] || (km == key[i] && om < off[i]);
-            rank[i] += lt ? 1 : 0;
+            for (int i = 0; i < S; ++i) rank[i] += km < key[i] ? 1 : 0;
         }
     }
 }
 
-// Final selection over the first nslots lane-strided slots, nb of which are
-// members (non-members carry key +inf and rank after every member):
-// FP64 refinement at the K-th boundary, then write ranks < K.
-template <int N>
-__device__ void select_and_write(const RerankParams& P, const float* ref, double (&key)[N],
-                                 int (&off)[N], int nslots, int nb, int lane, size_t r,
+__device__ __forceinline__ unsigned orderable(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Final selection: members carry key (float(d32) bits << 32 | offset);
+// non-members carry kNone.  FP64 refinement at the K-th boundary, then write
+// ranks < K (and the padding).
+template <int S>
+__device__ void select_and_write(const RerankParams& P, const float* ref,
+                                 const unsigned long long (&key)[S], int nb, int lane, size_t r,
                                  float gamma) {
-    int rank[N];
-    rank_members(key, off, nslots, lane, rank);
-    if (nb > P.K) {
-        // distances at ranks K-1 (last in) and K (first out), broadcast to the warp
-        double din = 0.0, dout = 0.0;
+    int rank[S];
+    warp_rank(key, rank);
+    double d64[S];
+    bool refined[S];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const bool m = lane + 32 * i < nslots;
-            din += (m && rank[i] == P.K - 1) ? key[i] : 0.0;
-            dout += (m && rank[i] == P.K) ? key[i] : 0.0;
+    for (int i = 0; i < S; ++i) {
+        refined[i] = false;
+        d64[i] = 0.0;
+    }
+    if (nb > P.K) {
+        float din = 0.f, dout = 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const float d = __uint_as_float((unsigned)(key[i] >> 32));
+            if (rank[i] == P.K - 1) din = d;
+            if (rank[i] == P.K) dout = d;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            din += __shfl_xor_sync(0xffffffffu, din, o);
-            dout += __shfl_xor_sync(0xffffffffu, dout, o);
+            din = fmaxf(din, __shfl_xor_sync(0xffffffffu, din, o));
+            dout = fmaxf(dout, __shfl_xor_sync(0xffffffffu, dout, o));
         }
-        const double tol = (double)gamma * (din + dout);
+        const float tol = gamma * (din + dout);
         if (dout - din <= tol) {
+            // boundary members: FP64 distances decide their order
             int nrec = 0;
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int m = lane + 32 * i;
-                if (m < nslots && rank[i] < nb && key[i] >= din - 2.0 * tol &&
-                    key[i] <= dout + 2.0 * tol) {
-                    key[i] = direct_f64(P, ref, off[i] / P.W, off[i] % P.W);
+            for (int i = 0; i < S; ++i) {
+                const float d = __uint_as_float((unsigned)(key[i] >> 32));
+                if (key[i] != kNone && d >= din - 2.f * tol && d <= dout + 2.f * tol) {
+                    const int off = (int)(unsigned)(key[i] & 0xffffffffu);
+                    d64[i] = direct_f64(P, ref, off / P.W, off % P.W);
+                    refined[i] = true;
                     ++nrec;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
             if (lane == 0 && nrec) atomicAdd(P.counters + 1, (unsigned long long)nrec);
-            rank_members(key, off, nslots, lane, rank);
+            // The refined members occupy a contiguous range of ranks (they are
+            // exactly the members whose FP32 distance lies in the boundary
+            // interval); re-rank them among themselves by (FP64 distance, offset).
+            int start = INT_MAX;
+#pragma unroll
+            for (int i = 0; i < S; ++i)
+                if (refined[i]) start = min(start, rank[i]);
+            for (int o = 16; o > 0; o >>= 1) start = min(start, __shfl_xor_sync(0xffffffffu, start, o));
+            int sub[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) sub[i] = 0;
+#pragma unroll
+            for (int slot = 0; slot < S; ++slot) {
+                for (int src = 0; src < 32; ++src) {
+                    const int rm = __shfl_sync(0xffffffffu, refined[slot] ? 1 : 0, src);
+                    const double dm = __shfl_sync(0xffffffffu, d64[slot], src);
+                    const unsigned long long km = __shfl_sync(0xffffffffu, key[slot], src);
+                    if (!rm) continue;
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        const bool before =
+                            dm < d64[i] ||
+                            (dm == d64[i] && (km & 0xffffffffull) < (key[i] & 0xffffffffull));
+                        sub[i] += (refined[i] && before) ? 1 : 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < S; ++i)
+                if (refined[i]) rank[i] = start + sub[i];
         }
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const int m = lane + 32 * i;
-        if (m < nslots && rank[i] < nb && rank[i] < P.K) {
-            P.out_idx[r * P.K + rank[i]] = off[i];
-            P.out_dist[r * P.K + rank[i]] = (float)key[i];
+    for (int i = 0; i < S; ++i) {
+        if (key[i] != kNone && rank[i] < P.K) {
+            P.out_idx[r * P.K + rank[i]] = (int32_t)(unsigned)(key[i] & 0xffffffffu);
+            P.out_dist[r * P.K + rank[i]] =
+                refined[i] ? (float)d64[i] : __uint_as_float((unsigned)(key[i] >> 32));
         }
     }
     for (int k = nb + lane; k < P.K; k += 32) {
@@ -160,6 +185,7 @@ __device__ void select_and_write(const RerankParams& P, const float* ref, double
     }
 }
 
+template <int S>
 __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_constant__ RerankParams P) {
     __shared__ float ref_s[kWarps][kMaxPatchElems];
     __shared__ unsigned long long list_s[kWarps][kFbSlots * 32];
@@ -179,12 +205,11 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     const float gamma = (float)(pc * P.p + 3) * 5.9604645e-08f;  // (n + 3) 2^-24
 
     // ---- load the pool (any order; empty slots have offset -1)
-    float v[kSlots];
-    int off[kSlots];
-    float nc[kSlots];
+    float v[S], nc[S];
+    int off[S];
     int npool = 0;
 #pragma unroll
-    for (int i = 0; i < kSlots; ++i) {
+    for (int i = 0; i < S; ++i) {
         const int k = lane + 32 * i;
         v[i] = -__int_as_float(0x7f800000);
         off[i] = -1;
@@ -201,31 +226,22 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     for (int o = 16; o > 0; o >>= 1) npool += __shfl_xor_sync(0xffffffffu, npool, o);
 
     // ---- band: entries with v >= T' (see the file header)
-    bool member[kSlots];
+    bool member[S];
 #pragma unroll
-    for (int i = 0; i < kSlots; ++i) member[i] = off[i] >= 0;
+    for (int i = 0; i < S; ++i) member[i] = off[i] >= 0;
     int nb = npool;
     bool overflow = false;
     if (npool > P.K) {
-        // rank of every entry by v descending (ties: slot order)
-        int rk[kSlots];
+        // rank by v descending (ties: slot index)
+        unsigned long long vk[S];
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) rk[i] = 0;
-        for (int m = 0; m < P.L; ++m) {
-            const int src = m & 31, slot = m >> 5;
-            float vm = v[0];
-#pragma unroll
-            for (int k = 1; k < kSlots; ++k) vm = slot == k ? v[k] : vm;
-            vm = __shfl_sync(0xffffffffu, vm, src);
-#pragma unroll
-            for (int i = 0; i < kSlots; ++i) {
-                const int me = lane + 32 * i;
-                rk[i] += (vm > v[i] || (vm == v[i] && m < me)) ? 1 : 0;
-            }
-        }
+        for (int i = 0; i < S; ++i)
+            vk[i] = ((unsigned long long)(~orderable(v[i])) << 32) | (unsigned)(lane + 32 * i);
+        int rk[S];
+        warp_rank(vk, rk);
         float vK = -__int_as_float(0x7f800000), ncmax = 0.f;
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) {
+        for (int i = 0; i < S; ++i) {
             if (off[i] >= 0 && rk[i] == P.K - 1) vK = v[i];
             if (off[i] >= 0 && rk[i] < P.K) ncmax = fmaxf(ncmax, nc[i]);
         }
@@ -236,7 +252,7 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         const float tb = vK - 2.0f * kEps * (nr + ncmax) * 1.0001f;
         int cnt = 0;
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) {
+        for (int i = 0; i < S; ++i) {
             member[i] = off[i] >= 0 && v[i] >= tb;
             cnt += member[i] ? 1 : 0;
         }
@@ -246,24 +262,24 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     }
 
     if (!overflow) {
-        double key[kSlots];
+        unsigned long long key[S];
         int viol = 0;
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) {
-            key[i] = __longlong_as_double(0x7ff0000000000000ll);  // +inf: not a member
+        for (int i = 0; i < S; ++i) {
+            key[i] = kNone;
             if (member[i]) {
                 const float d32 = direct_f32(P, ref, off[i] / P.W, off[i] % P.W);
-                key[i] = d32;
+                key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)off[i];
                 // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
                 const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
-                if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f) ++viol;
-            } else {
-                off[i] = 0x7fffffff;
+                if (fabsf(dt - d32) >
+                    2.0f * kEps * (nr + nc[i]) + gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
+                    ++viol;
             }
         }
         for (int o = 16; o > 0; o >>= 1) viol += __shfl_xor_sync(0xffffffffu, viol, o);
         if (lane == 0 && viol) atomicAdd(P.counters + 2, (unsigned long long)viol);
-        select_and_write(P, ref, key, off, P.L, nb, lane, r, gamma);
+        select_and_write<S>(P, ref, key, nb, lane, r, gamma);
         return;
     }
 
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     if (lane == 0) atomicAdd(P.counters + 0, 1ull);
     unsigned long long* list = list_s[warp];
     const int nl = P.K + 1;
-    for (int e = lane; e < kFbSlots * 32; e += 32) list[e] = ~0ull;
+    for (int e = lane; e < kFbSlots * 32; e += 32) list[e] = kNone;
     __syncwarp();
     const int Hc = P.H - P.p + 1;
     const int y0 = max(0, yr - P.h), y1 = min(Hc - 1, yr + P.h);
@@ -280,26 +296,26 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
     const int total = (y1 - y0 + 1) * nxw;
     for (int base = 0; base < total; base += 32) {
         const int i = base + lane;
-        unsigned long long key = ~0ull;
+        unsigned long long k = kNone;
         if (i < total) {
             const int yc = y0 + i / nxw, xc = x0 + i % nxw;
             const float d = direct_f32(P, ref, yc, xc);
-            key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * P.W + xc);
+            k = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * P.W + xc);
         }
-        unsigned pass = __ballot_sync(0xffffffffu, key < list[nl - 1]);
+        unsigned pass = __ballot_sync(0xffffffffu, k < list[nl - 1]);
         while (pass) {
             const int src = __ffs(pass) - 1;
             pass &= pass - 1;
-            const unsigned long long k = __shfl_sync(0xffffffffu, key, src);
-            if (!(k < list[nl - 1])) continue;
+            const unsigned long long kk = __shfl_sync(0xffffffffu, k, src);
+            if (!(kk < list[nl - 1])) continue;
             int pos = 0;
-            for (int e = lane; e < nl; e += 32) pos += list[e] < k ? 1 : 0;
+            for (int e = lane; e < nl; e += 32) pos += list[e] < kk ? 1 : 0;
             for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
             unsigned long long nv[kFbSlots];
 #pragma unroll
             for (int t = 0; t < kFbSlots; ++t) {
                 const int e = lane + 32 * t;
-                nv[t] = e < nl ? (e > pos ? list[e - 1] : (e == pos ? k : list[e])) : ~0ull;
+                nv[t] = e < nl ? (e > pos ? list[e - 1] : (e == pos ? kk : list[e])) : kNone;
             }
             __syncwarp();
 #pragma unroll
@@ -308,19 +324,16 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
             __syncwarp();
         }
     }
-    double key2[kFbSlots];
-    int off2[kFbSlots];
+    unsigned long long key2[kFbSlots];
     int cnt = 0;
 #pragma unroll
     for (int t = 0; t < kFbSlots; ++t) {
         const int e = lane + 32 * t;
-        const unsigned long long k = e < nl ? list[e] : ~0ull;
-        key2[t] = k == ~0ull ? 0.0 : (double)__uint_as_float((unsigned)(k >> 32));
-        off2[t] = k == ~0ull ? -1 : (int)(unsigned)(k & 0xffffffffu);
-        cnt += (k != ~0ull) ? 1 : 0;
+        key2[t] = e < nl ? list[e] : kNone;
+        cnt += key2[t] != kNone ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    select_and_write(P, ref, key2, off2, cnt, cnt, lane, r, gamma);
+    select_and_write<kFbSlots>(P, ref, key2, cnt, lane, r, gamma);
 }
 
 }  // namespace
@@ -328,14 +341,20 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
 cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
                           const int32_t* pool_idx, const float* pool_score, int32_t* out_idx,
                           float* out_dist, unsigned long long* counters, cudaStream_t st) {
-    if (g.L > kMaxPool) return cudaErrorNotSupported;
     RerankParams P{};
     P.img = img; P.nrm = nrm; P.pool_idx = pool_idx; P.pool_score = pool_score;
     P.out_idx = out_idx; P.out_dist = out_dist; P.counters = counters;
     P.H = g.H; P.W = g.W; P.C = g.C; P.p = g.p; P.h = g.h; P.s = g.s; P.K = g.K; P.L = g.L;
     P.n_ry = g.n_ry; P.n_rx = g.n_rx; P.Wc = g.Wc; P.nR = g.nR;
     const int blocks = (g.nR + kWarps - 1) / kWarps;
-    rerank_kernel<<<blocks, kWarps * 32, 0, st>>>(P);
+    switch ((g.L + 31) / 32) {
+        case 1: rerank_kernel<1><<<blocks, kWarps * 32, 0, st>>>(P); break;
+        case 2: rerank_kernel<2><<<blocks, kWarps * 32, 0, st>>>(P); break;
+        case 3: rerank_kernel<3><<<blocks, kWarps * 32, 0, st>>>(P); break;
+        case 4: rerank_kernel<4><<<blocks, kWarps * 32, 0, st>>>(P); break;
+        case 5: rerank_kernel<5><<<blocks, kWarps * 32, 0, st>>>(P); break;
+        default: return cudaErrorNotSupported;
+    }
     return cudaGetLastError();
 }
 

@@ -15,10 +15,11 @@
 // extra K-step of the same MMA (A = constant coefficients, B = n_j split into
 // three bf16 pieces), so TMEM already holds the score.
 //
-//   uint8 : bf16 operands are exact (0..255), products and all partial sums
-//           are integers below 2^24, so the FP32 accumulation is exact; the
-//           norm term is floor(n_j / 2) with coefficient -1 and the parity of
-//           n_j is restored in the exact key d = n_r - 2 v + (n_j & 1).
+//   uint8 : operands are centred (x - 128) and A is doubled, all exact in
+//           bf16; products and every partial sum are integers below 2^24
+//           (p*p*C <= 256), so the FP32 accumulation is exact in any order.
+//           The norm K-step uses coefficient -1, so TMEM holds the exact
+//           integer v = 2 <X_r, X_j> - n_j and d = n_r - v.
 //           Output: the final K (index, distance) per reference.
 //   float32: x = hi + lo (bf16 each); cross term = hi.hi + hi.lo + lo.hi; norm
 //           coefficient -0.5 plus +eps on a second copy of the pieces, so
@@ -37,9 +38,11 @@
 // every K-step is a plain descriptor with SBO = 128 B and LBO = 16 B (next
 // patch row) or the q-strip pitch (next chunk of the same row).
 //
-// Warp roles (288 threads): warps 0-3 epilogue (TMEM lanes 32w..32w+31 =
-// reference row w of the tile), warps 4-7 producers (strip formation from
-// the bf16 planes), warp 8 TMEM allocation + single-thread MMA issue.
+// Warp roles: warps 0..EW-1 epilogue (warp w reads TMEM lanes 32(w%4)..+31;
+// with EW = 8 two warps share each lane quarter and take alternate candidate
+// columns, each keeping its own list, merged at the end of the tile), the
+// next three warps producers (strip formation from the bf16 planes), the last
+// warp TMEM allocation + single-thread MMA issue.
 // Pipelines: kStages shared-memory stages (mbarriers full/empty) and two
 // 256-column TMEM accumulators (tfull/tempty).  Every wait is bounded; on
 // timeout the CTA sets *status, drains and frees its TMEM.
@@ -50,8 +53,10 @@
 namespace bm {
 namespace {
 
-constexpr int kThreads = 288;
-constexpr int kMmaWarp = 8;
+constexpr int kProducers = 96;  // three producer warps
+// Threads of a CTA with EW epilogue warps: EW + 3 producer warps + 1 MMA warp.
+template <int EW>
+__host__ __device__ constexpr int cta_threads() { return EW * 32 + kProducers + 32; }
 constexpr int kStages = 3;
 constexpr int kTmemCols = 512;
 constexpr int kBufCols = 256;
@@ -59,7 +64,8 @@ constexpr float kEps = 6.103515625e-05f;  // 2^-14
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kBuf = 32;  // per-lane append buffer (entries) between heap merges
+constexpr int kBuf = 32;   // per-lane append buffer (entries) between merges
+constexpr int kBatch = 8;  // keys merged into the register list at a time
 
 struct TcGeom {
     int H, W, Cp, p, h, s, K, HL, n_ry, n_rx, Hc, Wc;
@@ -313,10 +319,47 @@ struct Heap {
     }
 };
 
-// Register-resident sorted list of the best keys (ascending), capacity LC,
-// of which the first `cap` entries are used.  insert() is a branch-free
-// insertion network: a key that is not better than entry cap-1 changes
-// nothing, so every lane of a warp can run it in lock-step.
+// Compare-exchange: x <- min, y <- max.
+__device__ __forceinline__ void cmpx(unsigned long long& x, unsigned long long& y) {
+    const bool s = y < x;
+    const unsigned long long lo = s ? y : x, hi = s ? x : y;
+    x = lo;
+    y = hi;
+}
+// Bitonic sort of N registers, ascending.
+template <int N>
+__device__ __forceinline__ void bitonic_sort(unsigned long long (&v)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    if ((i & k) == 0) cmpx(v[i], v[l]);
+                    else cmpx(v[l], v[i]);
+                }
+            }
+}
+// Sort a bitonic sequence of N registers, ascending.
+template <int N>
+__device__ __forceinline__ void bitonic_merge(unsigned long long (&v)[N]) {
+#pragma unroll
+    for (int j = N >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int l = i ^ j;
+            if (l > i) cmpx(v[i], v[l]);
+        }
+}
+
+// Register-resident sorted list (ascending) of the LC best keys.  New keys
+// arrive in batches of kBatch: the batch is bitonic-sorted, the LC smallest
+// of list + batch are min(a[i], batch[LC-1-i]) (a bitonic sequence), and one
+// bitonic merge restores the order -- far fewer compare-exchanges per key
+// than a full insertion pass per key.  Entries 0..cap-1 are the
+// answer (cap <= LC); extra entries only make the list a superset.
 template <int LC>
 struct RegTopK {
     unsigned long long a[LC];
@@ -326,16 +369,16 @@ struct RegTopK {
 #pragma unroll
         for (int i = 0; i < LC; ++i) a[i] = kEmpty;
     }
-    __device__ __forceinline__ void insert(unsigned long long k) {
-        bool lt[LC];
+    __device__ __forceinline__ void merge_batch(unsigned long long (&b)[kBatch]) {
+        bitonic_sort<kBatch>(b);
 #pragma unroll
-        for (int i = 0; i < LC; ++i) lt[i] = k < a[i];
-#pragma unroll
-        for (int i = LC - 1; i > 0; --i)
-            if (i < cap) a[i] = lt[i - 1] ? a[i - 1] : (lt[i] ? k : a[i]);
-        a[0] = lt[0] ? k : a[0];
+        for (int i = 0; i < LC; ++i) {
+            const int bi = LC - 1 - i;
+            if (bi < kBatch) a[i] = b[bi] < a[i] ? b[bi] : a[i];
+        }
+        bitonic_merge<LC>(a);
     }
-    __device__ __forceinline__ unsigned long long kth() const {  // entry cap-1 (the largest used)
+    __device__ __forceinline__ unsigned long long kth() const {  // entry cap-1
         unsigned long long r = 0;
 #pragma unroll
         for (int i = 0; i < LC; ++i) {
@@ -348,51 +391,60 @@ struct RegTopK {
 
 // Warp-synchronous merge of every lane's pending entries (call from all 32
 // lanes): one pending entry per lane per step goes through the selection.
-template <int LC>
+template <int LC, bool kF32, int PS>
 __device__ __forceinline__ void merge_pending(const TcGeom& G, const int* nrm_i, int nr_i,
                                               unsigned long long* pend, int& cnt, float& thr,
                                               RegTopK<LC == 0 ? 1 : LC>& reg, Heap& heap) {
     const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
-    for (int j0 = 0; j0 < m; j0 += 4) {
-        unsigned long long e[4];
-        int par[4];
+    for (int j0 = 0; j0 < m; j0 += kBatch) {
+        unsigned long long b[kBatch];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kBatch; ++t) {
             const int j = j0 + t;
-            e[t] = j < cnt ? pend[j * 128] : kEmpty;
-            par[t] = 0;
-            if (!G.f32 && j < cnt) {
-                const unsigned off = (unsigned)(e[t] & 0xffffffffu);
-                const unsigned yc = off / (unsigned)G.W, xc = off - yc * (unsigned)G.W;
-                par[t] = nrm_i[(size_t)yc * G.Wc + xc] & 1;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
+            const unsigned long long e = j < cnt ? pend[j * PS] : kEmpty;
             unsigned long long key = kEmpty;
-            if (e[t] != kEmpty) {
-                const float v = __uint_as_float((unsigned)(e[t] >> 32));
-                const unsigned long long off = e[t] & 0xffffffffull;
-                if (G.f32) {
+            if (e != kEmpty) {
+                const float v = __uint_as_float((unsigned)(e >> 32));
+                const unsigned long long off = e & 0xffffffffull;
+                if (kF32) {
                     key = ((unsigned long long)(~orderable(v)) << 32) | off;
                 } else {
-                    const int dd = nr_i - 2 * (int)v + par[t];
+                    const int dd = nr_i - (int)v;  // v = 2 <X_r, X_j> - ||X_j||^2, exact
                     key = ((unsigned long long)(unsigned)dd << 32) | off;
                 }
             }
-            if (LC > 0) {
-                reg.insert(key);
-            } else if (key < heap.top()) {
-                heap.replace_top(key);
-            }
+            b[t] = key;
+        }
+        if constexpr (LC > 0) {
+            reg.merge_batch(b);
+        } else {
+#pragma unroll 1
+            for (int t = 0; t < kBatch; ++t)
+                if (b[t] < heap.top()) heap.replace_top(b[t]);
         }
     }
     cnt = 0;
-    const unsigned long long t = LC > 0 ? reg.kth() : heap.top();
+    unsigned long long t;
+    if constexpr (LC > 0) t = reg.kth();
+    else t = heap.top();
     if (t != kEmpty) {
-        if (G.f32) thr = from_orderable(~(unsigned)(t >> 32));
-        else thr = (float)((nr_i - (int)(t >> 32)) >> 1) - 1.0f;
+        if (kF32) thr = from_orderable(~(unsigned)(t >> 32));
+        else thr = (float)(nr_i - (int)(t >> 32));  // v >= thr  <=>  d <= d_K (exact)
     }
+}
+
+// Final flush of the pending entries, out of line (runs once per tile, so
+// it stays out of the hot loop's instruction footprint).  The register list
+// travels by value.
+template <int LC, bool kF32, int PS>
+__device__ __noinline__ RegTopK<LC == 0 ? 1 : LC> final_merge(const TcGeom G, const int* nrm_i,
+                                                             int nr_i, unsigned long long* pend,
+                                                             int cnt, RegTopK<LC == 0 ? 1 : LC> reg,
+                                                             unsigned long long* heap_h) {
+    float thr = 0.f;
+    Heap heap{heap_h, G.HL};
+    merge_pending<LC, kF32, PS>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+    return reg;
 }
 
 // Chunk visiting order: centre-first.  Chunk 0 holds the candidate columns
@@ -410,10 +462,17 @@ __device__ __forceinline__ int chunk_order(int c, int n, int cc) {
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int LC>  // register list capacity (16, 32), or 0 for the shared-memory heap
-__global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_constant__ TcParams P) {
+// LC: register list capacity (16, 32), or 0 for the shared-memory heap.
+// F32: float32 input (split operands, pool output) or uint8 (exact output).
+template <int LC, bool F32, int EW>
+__global__ void __launch_bounds__(cta_threads<EW>(), 1)
+tc_match_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcGeom& G = P.g;
+    constexpr bool kF32 = F32;
+    constexpr int kThreads = cta_threads<EW>();
+    constexpr int kMmaWarp = EW + 3;
+    constexpr int kEpi = EW * 32;  // epilogue threads (pending-buffer stride)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int ry0 = blockIdx.y * G.ty, rx0 = blockIdx.x * G.tx;
@@ -434,12 +493,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
-            mbar_init(bar_full + 8 * i, 128);
+            mbar_init(bar_full + 8 * i, kProducers);
             mbar_init(bar_empty + 8 * i, 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar_tfull + 8 * i, 1);
-            mbar_init(bar_tempty + 8 * i, 128);
+            mbar_init(bar_tempty + 8 * i, kEpi);
         }
         mbar_init(bar_done, 1);
         *abort_flag = 0;
@@ -449,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
 
     // ---- A: reference patches, K-major core matrices [group][kchunk][8 rows x 16 B]
     {
-        const int nplanes = G.f32 ? 2 : 1;
+        const int nplanes = kF32 ? 2 : 1;
         const int items = 128 * G.nkc;
         for (int t = threadIdx.x; t < items * nplanes; t += kThreads) {
             const int pl = t / items, it = t % items;
@@ -475,6 +534,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                     val = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
+            if (!kF32) {
+                // uint8: A = 2 (x - 128), exact in bf16, so the MMA yields 2 <X_r, X_j>
+                uint32_t w[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
+                    const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
+                    w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
+                }
+                val = make_uint4(w[0], w[1], w[2], w[3]);
+            }
             uint8_t* base = smem + (pl ? G.off_a1 : G.off_a0);
             *reinterpret_cast<uint4*>(base + (size_t)(m >> 3) * G.nkc * 128 + kc * 128 +
                                       (m & 7) * 16) = val;
@@ -484,9 +554,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             const int m = t >> 1, kc = t & 1;
             uint16_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (kc == 0) {
-                const uint16_t cn = bf16_bits(G.f32 ? -0.5f : -1.0f);
+                const uint16_t cn = bf16_bits(kF32 ? -0.5f : -1.0f);
                 c[0] = c[1] = c[2] = cn;
-                if (G.f32) c[3] = c[4] = c[5] = bf16_bits(kEps);
+                if (kF32) c[3] = c[4] = c[5] = bf16_bits(kEps);
             }
             uint4 val = make_uint4(c[0] | (uint32_t(c[1]) << 16), c[2] | (uint32_t(c[3]) << 16),
                                    c[4] | (uint32_t(c[5]) << 16), c[6] | (uint32_t(c[7]) << 16));
@@ -497,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
     for (int t = threadIdx.x; t < kStages * G.stage_bytes / 16; t += kThreads)
         reinterpret_cast<uint4*>(smem + G.off_stage)[t] = make_uint4(0, 0, 0, 0);
     // epilogue threads: empty heaps
-    if (threadIdx.x < 128) {
+    if (LC == 0 && threadIdx.x < 128) {
         unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + G.off_heap) + threadIdx.x;
         for (int i = 0; i < G.HL; ++i) h[i * 128] = kEmpty;
     }
@@ -507,10 +577,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= EW && warp < kMmaWarp) {
         // ------------------------------------------------------------ producers
-        const int pt = threadIdx.x - 128;
-        const int nplanes = G.f32 ? 2 : 1;
+        const int pt = threadIdx.x - kEpi;
+        const int nplanes = kF32 ? 2 : 1;
         const int strip_items = nplanes * G.pw * G.kcols * G.Rb;
         const int norm_items = G.kcols * G.Rb;
         const int* nrm_i = static_cast<const int*>(P.nrm);
@@ -521,12 +591,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             uint8_t* sb = smem + G.off_stage + stage * G.stage_bytes;
             const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
             const int kc_here = min(G.kcols, NX - jc0);
-            for (int t0 = pt; t0 < strip_items; t0 += 4 * 128) {
+            for (int t0 = pt; t0 < strip_items; t0 += 4 * kProducers) {
                 uint4 val[4];
                 int dst[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int t = t0 + k * 128;
+                    const int t = t0 + k * kProducers;
                     dst[k] = -1;
                     val[k] = make_uint4(0, 0, 0, 0);
                     if (t >= strip_items) continue;
@@ -548,19 +618,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                     if (dst[k] >= 0) *reinterpret_cast<uint4*>(sb + dst[k]) = val[k];
             }
             uint8_t* nsb = sb + nplanes * G.plane_stage;
-            for (int t = pt; t < norm_items; t += 128) {
+            for (int t = pt; t < norm_items; t += kProducers) {
                 const int row = t % G.Rb, jl = t / G.Rb;
                 if (jl >= kc_here) continue;
                 uint16_t hi = 0, mid = 0, lo = 0;
                 if (row < NR) {
                     const size_t ni = (size_t)(Y0 + row) * G.Wc + (X0 + jc0 + jl);
-                    const float w = G.f32 ? nrm_f[ni] : (float)(nrm_i[ni] >> 1);
+                    const float w = kF32 ? nrm_f[ni] : (float)nrm_i[ni];
                     split3(w, hi, mid, lo);
                 } else {
                     hi = bf16_bits(1.0e18f);  // no real candidate: never selected
                 }
                 uint4 val;
-                if (G.f32) {
+                if (kF32) {
                     val = make_uint4(hi | (uint32_t(mid) << 16), lo | (uint32_t(hi) << 16),
                                      mid | (uint32_t(lo) << 16), 0u);
                 } else {
@@ -577,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             const uint32_t a0 = smem_u32(smem + G.off_a0), a1 = smem_u32(smem + G.off_a1);
             const uint32_t an = smem_u32(smem + G.off_an);
             const uint32_t sbo_a = G.nkc * 128;
-            const int nplanes = G.f32 ? 2 : 1;
+            const int nplanes = kF32 ? 2 : 1;
             const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
             int c = 0;
             for (; c < nchunks; ++c) {
@@ -626,22 +696,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
         // threshold are appended with predicated stores (no divergent work);
         // when any lane's buffer nears full the whole warp merges its buffers
         // into the heaps in lock-step.
-        Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + threadIdx.x, G.HL};
+        const int quarter = warp & 3, half = warp >> 2;
+        Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + (threadIdx.x & 127), G.HL};
         RegTopK<LC == 0 ? 1 : LC> reg;
         reg.init(G.HL);
         unsigned long long* pend = reinterpret_cast<unsigned long long*>(smem + G.off_buf) + threadIdx.x;
-        const int ry = ry0 + (warp / G.wgx) * G.rr + lane / G.rc;
-        const int rx = rx0 + (warp % G.wgx) * G.rc + lane % G.rc;
+        const int ry = ry0 + (quarter / G.wgx) * G.rr + lane / G.rc;
+        const int rx = rx0 + (quarter % G.wgx) * G.rc + lane % G.rc;
         const bool lane_ok = ry < G.n_ry && rx < G.n_rx;
         const int yr = ry * G.s, xr = rx * G.s;
         // this lane's candidate rows inside the strip (empty if the lane has no reference)
         const int lo = lane_ok ? max(0, yr - G.h - Y0) : 1 << 20;
         const int hi = lane_ok ? min(NR - 1, yr + G.h - Y0) : -1;
         const int* nrm_i = static_cast<const int*>(P.nrm);
-        const int nr_i = (lane_ok && !G.f32) ? nrm_i[(size_t)yr * G.Wc + xr] : 0;
+        const int nr_i = (lane_ok && !kF32) ? nrm_i[(size_t)yr * G.Wc + xr] : 0;
         float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
         int cnt = 0;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         for (int c = 0; c < nchunks; ++c) {
             const int buf = c & 1, ub = c >> 1;
             if (!mbar_wait(bar_tfull + 8 * buf, ub & 1, abort_flag, 4)) break;
@@ -649,6 +720,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
             const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
             const int kc_here = min(G.kcols, NX - jc0);
             for (int jl = 0; jl < kc_here; ++jl) {
+                if (EW == 8 && ((c * G.kcols + jl) & 1) != half) continue;  // partner's column
                 const int xc = X0 + jc0 + jl;
                 const bool xok = lane_ok && abs(xc - xr) <= G.h;
                 if (!__any_sync(0xffffffffu, xok)) continue;
@@ -657,18 +729,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                 const int whi = __reduce_max_sync(0xffffffffu, xok ? hi : -1);
                 const int b0 = wlo >> 4, nblk = (whi >> 4) - b0 + 1;
                 const uint32_t colbase = tmem_base + lane_base + buf * kBufCols + jl * G.Rb + 16 * b0;
-                for (int bb = 0; bb < nblk; bb += 2) {
-                    const int nb = min(2, nblk - bb);
-                    float v[32];
-                    if (nb == 2) tmem_ld_blocks<2>(colbase + 16 * bb, v);
-                    else tmem_ld_blocks<1>(colbase + 16 * bb, v);
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        if (t >= nb) break;
-                        const int b = b0 + bb + t;
+                for (int bb = 0; bb < nblk; ++bb) {
+                    float w[16];
+                    tmem_ld_blocks<1>(colbase + 16 * bb, w);
+                    {
+                        const int b = b0 + bb;
                         // this lane's valid rows of block b: [i0, i1] (may be empty)
                         const int i0 = lo - 16 * b, i1 = xok ? hi - 16 * b : -1;
-                        const float* w = v + 16 * t;
                         const float ninf = -__int_as_float(0x7f800000);
                         float m = ninf;
 #pragma unroll
@@ -678,35 +745,57 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                             m = max3(m, a, c2);
                         }
                         const bool hit = m >= thr;
-                        if (!__any_sync(0xffffffffu, hit)) continue;
-                        if (__any_sync(0xffffffffu, cnt > kBuf - 16))
-                            merge_pending<LC>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+                        if (!__any_sync(0xffffffffu, hit)) continue;  // next block
                         if (hit) {
                             const int ybase = Y0 + 16 * b;
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
                                 if (i >= i0 && i <= i1 && w[i] >= thr) {
-                                    pend[cnt * 128] =
+                                    pend[cnt * kEpi] =
                                         ((unsigned long long)__float_as_uint(w[i]) << 32) |
                                         (unsigned)((ybase + i) * G.W + xc);
                                     ++cnt;
                                 }
                             }
                         }
+                        // keep room for the next block's appends
+                        if (__any_sync(0xffffffffu, cnt > kBuf - 16))
+                            merge_pending<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(bar_tempty + 8 * buf);
         }
-        merge_pending<LC>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+        if (__any_sync(0xffffffffu, cnt > 0))
+            reg = final_merge<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
+        if constexpr (EW == 8 && LC > 0) {
+            // combine the two half-lists of each lane quarter: warps 4-7 hand
+            // their keys to warps 0-3 through the pending buffers
+            asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
+            if (half == 1) {
+#pragma unroll
+                for (int i = 0; i < LC; ++i) pend[i * kEpi] = reg.a[i];
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
+            if (half == 0) {
+                const unsigned long long* other = pend + 128;
+#pragma unroll 1
+                for (int j0 = 0; j0 < LC; j0 += kBatch) {
+                    unsigned long long b[kBatch];
+#pragma unroll
+                    for (int t = 0; t < kBatch; ++t) b[t] = other[(j0 + t) * kEpi];
+                    reg.merge_batch(b);
+                }
+            }
+        }
         // ---- write results
-        if (lane_ok && !*abort_flag) {
+        if (half == 0 && lane_ok && !*abort_flag) {
             const size_t ref = (size_t)ry * G.n_rx + rx;
-            if (LC == 0 && !G.f32) heap.sort();
-            const int nout = G.f32 ? G.HL : G.K;
+            if constexpr (LC == 0 && !kF32) heap.sort();
+            const int nout = kF32 ? G.HL : G.K;
             auto emit = [&](int k, unsigned long long key) {
-                if (G.f32) {
+                if (kF32) {
                     // pool: any order; the re-rank kernel ranks it
                     P.pool_idx[ref * G.HL + k] = key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
                     P.pool_score[ref * G.HL + k] = key == kEmpty ? -__int_as_float(0x7f800000)
@@ -716,9 +805,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_match_kernel(const __grid_cons
                     P.out_dist[ref * G.K + k] = key == kEmpty ? 0x7fffffff : (int32_t)(unsigned)(key >> 32);
                 }
             };
-            if (LC > 0) {
+            if constexpr (LC > 0) {
 #pragma unroll
-                for (int i = 0; i < (LC == 0 ? 1 : LC); ++i)
+                for (int i = 0; i < LC; ++i)
                     if (i < nout) emit(i, reg.a[i]);
             } else {
                 for (int k = 0; k < nout; ++k) emit(k, heap.h[k * 128]);
@@ -774,8 +863,9 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
     t.off_a1 = off; off += t.f32 ? a_bytes : 0;
     t.off_an = off; off += 128 * 2 * 16;
     t.off_stage = off; off += kStages * t.stage_bytes;
-    t.off_heap = off; off += 128 * t.HL * 8;
-    t.off_buf = off; off += 128 * kBuf * 8;
+    const int ew = t.HL <= 32 ? 8 : 4;  // epilogue warps (the shared-memory heap keeps 4)
+    t.off_heap = off; off += t.HL > 32 ? 128 * t.HL * 8 : 0;
+    t.off_buf = off; off += ew * 32 * kBuf * 8;
     t.off_bar = off; off += (2 * kStages + 5) * 8 + 16;
     t.smem_total = (off + 1023) / 1024 * 1024;
     // the plane padding covers the widest read (see make_geom)
@@ -803,10 +893,18 @@ cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {
     // at least 114 KB of shared memory keeps one CTA per SM (whole-TMEM allocation)
     const int smem = P.g.smem_total < 116 * 1024 ? 116 * 1024 : P.g.smem_total;
     dim3 grid((g.n_rx + P.g.tx - 1) / P.g.tx, (g.n_ry + P.g.ty - 1) / P.g.ty);
-    auto kern = P.g.HL <= 16 ? tc_match_kernel<16> : P.g.HL <= 32 ? tc_match_kernel<32>
-                                                                  : tc_match_kernel<0>;
+    void (*kern)(TcParams);
+    int threads;
+    if (P.g.HL <= 32) {
+        threads = cta_threads<8>();
+        if (P.g.f32) kern = tc_match_kernel<32, true, 8>;
+        else kern = P.g.HL <= 16 ? tc_match_kernel<16, false, 8> : tc_match_kernel<32, false, 8>;
+    } else {
+        threads = cta_threads<4>();
+        kern = P.g.f32 ? tc_match_kernel<0, true, 4> : tc_match_kernel<0, false, 4>;
+    }
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, kThreads, smem, st>>>(P);
+    kern<<<grid, threads, smem, st>>>(P);
     return cudaGetLastError();
 }
 
