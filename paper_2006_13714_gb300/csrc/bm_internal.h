@@ -77,6 +77,10 @@ struct TcArgs {
     int* status;              // device error word (0 = ok)
 };
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
+// Several jobs in persistent launches (consecutive jobs of one class share a launch).
+cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st);
+bool tc_supported(const Geom& g);
+bool tc_same_class(const Geom& a, const Geom& b);
 
 // (a6) float32 boundary re-rank: direct recomputation of the pool's band,
 // FP64 only for ties at the K-th boundary; writes the final outputs.

@@ -67,26 +67,38 @@ constexpr int kSmemLimit = 227 * 1024;
 constexpr int kBuf = 32;   // per-lane append buffer (entries) between merges
 constexpr int kBatch = 8;  // keys merged into the register list at a time
 
+// Class-wide geometry of one launch (every job shares patch, window, stride,
+// K, channel padding and dtype; image sizes are per job).
 struct TcGeom {
-    int H, W, Cp, p, h, s, K, HL, n_ry, n_rx, Hc, Wc;
+    int Cp, p, h, s, K, HL;
     int rr, rc, wgx, ty, tx;  // lane -> reference mapping and tile shape (references)
     int pw, p_eff, nkc, Rb, kcols;
+    int nslots, bufcols;      // tiles in flight per CTA, TMEM columns per accumulator
     int qpitch, plane_stage, ns_bytes, stage_bytes;
-    int plane_pitch;
     int f32;
-    int off_a0, off_a1, off_an, off_stage, off_heap, off_buf, off_bar, smem_total;
+    int off_a, a_bytes, off_an, off_stage, off_heap, off_buf, off_bar, smem_total;
 };
 
-struct TcParams {
-    TcGeom g;
+// One image of a launch.
+struct TcJob {
     const uint16_t* plane0;
     const uint16_t* plane1;
     const void* nrm;
-    int32_t* out_idx;
-    int32_t* out_dist;
-    int32_t* pool_idx;
+    int32_t* out_idx;     // uint8: final indices
+    int32_t* out_dist;    // uint8: final distances
+    int32_t* pool_idx;    // float32: pool
     float* pool_score;
+    int H, W, n_ry, n_rx, Hc, Wc, plane_pitch;
+    int tiles_x, tile_begin;  // tiles along x; index of the job's first tile
+};
+
+constexpr int kMaxJobs = 160;  // jobs per launch (kept inline in the kernel parameters)
+
+struct TcParams {
+    TcGeom g;
+    int njobs, total_tiles;
     int* status;
+    TcJob jobs[kMaxJobs];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -461,34 +473,79 @@ __device__ __forceinline__ int chunk_order(int c, int n, int cc) {
     return left > right ? cc - m - rest : cc + m + rest;
 }
 
+// ---------------------------------------------------------------- tiles
+
+struct TileInfo {
+    const TcJob* job;
+    int ry0, rx0, ry_last, rx_last;
+    int Y0, X0, NR, NX, nchunks, center_chunk;
+};
+
+// Tile t of the launch: its job (binary search over the jobs' first tiles)
+// and the union of its references' clipped windows.
+__device__ __forceinline__ TileInfo tile_info(const TcParams& P, int t) {
+    const TcGeom& G = P.g;
+    int lo = 0, hi = P.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    TileInfo T;
+    T.job = &P.jobs[lo];
+    const TcJob& J = *T.job;
+    const int lt = t - J.tile_begin;
+    T.ry0 = (lt / J.tiles_x) * G.ty;
+    T.rx0 = (lt % J.tiles_x) * G.tx;
+    T.ry_last = min(T.ry0 + G.ty - 1, J.n_ry - 1);
+    T.rx_last = min(T.rx0 + G.tx - 1, J.n_rx - 1);
+    T.Y0 = max(0, T.ry0 * G.s - G.h);
+    const int Y1 = min(J.Hc - 1, T.ry_last * G.s + G.h);
+    T.X0 = max(0, T.rx0 * G.s - G.h);
+    const int X1 = min(J.Wc - 1, T.rx_last * G.s + G.h);
+    T.NR = Y1 - T.Y0 + 1;
+    T.NX = X1 - T.X0 + 1;
+    T.nchunks = (T.NX + G.kcols - 1) / G.kcols;
+    T.center_chunk = min(T.nchunks - 1, ((T.rx0 + T.rx_last) * G.s / 2 - T.X0) / G.kcols);
+    return T;
+}
+
+// Tile of slot k's g-th turn in CTA b (static round robin over the launch).
+__device__ __forceinline__ int slot_tile(int b, int g, int k, int nslots, int grid) {
+    return b + (g * nslots + k) * grid;
+}
+
 // ---------------------------------------------------------------- the kernel
-// LC: register list capacity (16, 32), or 0 for the shared-memory heap.
-// F32: float32 input (split operands, pool output) or uint8 (exact output).
-template <int LC, bool F32, int EW>
-__global__ void __launch_bounds__(cta_threads<EW>(), 1)
+//
+// Persistent: CTA b walks the tiles b, b + G, b + 2G, ... of every job of
+// the launch, NS tiles in flight ("slots").  Slot k owns epilogue warps
+// 4k..4k+3, its own A operand region and two TMEM accumulators; the
+// producers and the MMA thread alternate between the slots' chunks, so the
+// epilogue of one tile overlaps the MMAs of the other.
+template <int LC, bool F32, int NS>
+__global__ void __launch_bounds__(cta_threads<4 * NS>(), 1)
 tc_match_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcGeom& G = P.g;
     constexpr bool kF32 = F32;
+    constexpr int EW = 4 * NS;
     constexpr int kThreads = cta_threads<EW>();
     constexpr int kMmaWarp = EW + 3;
     constexpr int kEpi = EW * 32;  // epilogue threads (pending-buffer stride)
+    constexpr int nplanes = kF32 ? 2 : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    const int ry0 = blockIdx.y * G.ty, rx0 = blockIdx.x * G.tx;
-    const int ry_last = min(ry0 + G.ty - 1, G.n_ry - 1), rx_last = min(rx0 + G.tx - 1, G.n_rx - 1);
-    const int Y0 = max(0, ry0 * G.s - G.h), Y1 = min(G.Hc - 1, ry_last * G.s + G.h);
-    const int X0 = max(0, rx0 * G.s - G.h), X1 = min(G.Wc - 1, rx_last * G.s + G.h);
-    const int NR = Y1 - Y0 + 1, NX = X1 - X0 + 1;
-    const int nchunks = (NX + G.kcols - 1) / G.kcols;
-    const int center_chunk = min(nchunks - 1, ((rx0 + rx_last) * G.s / 2 - X0) / G.kcols);
+    const int grid = gridDim.x, cta = blockIdx.x;
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G.off_bar);
+    // barrier slots: full[kStages], empty[kStages], tfull[NS][2], tempty[NS][2],
+    // afull[NS], aempty[NS], done
     const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kStages);
     const uint32_t bar_tfull = smem_u32(bars + 2 * kStages);
-    const uint32_t bar_tempty = smem_u32(bars + 2 * kStages + 2);
-    const uint32_t bar_done = smem_u32(bars + 2 * kStages + 4);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+    const uint32_t bar_tempty = smem_u32(bars + 2 * kStages + 2 * NS);
+    const uint32_t bar_afull = smem_u32(bars + 2 * kStages + 4 * NS);
+    const uint32_t bar_aempty = smem_u32(bars + 2 * kStages + 5 * NS);
+    const uint32_t bar_done = smem_u32(bars + 2 * kStages + 6 * NS);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6 * NS + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     if (threadIdx.x == 0) {
@@ -496,81 +553,36 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             mbar_init(bar_full + 8 * i, kProducers);
             mbar_init(bar_empty + 8 * i, 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 2 * NS; ++i) {
             mbar_init(bar_tfull + 8 * i, 1);
-            mbar_init(bar_tempty + 8 * i, kEpi);
+            mbar_init(bar_tempty + 8 * i, 128);
+        }
+        for (int k = 0; k < NS; ++k) {
+            mbar_init(bar_afull + 8 * k, kProducers);
+            mbar_init(bar_aempty + 8 * k, 1);
         }
         mbar_init(bar_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
-
-    // ---- A: reference patches, K-major core matrices [group][kchunk][8 rows x 16 B]
-    {
-        const int nplanes = kF32 ? 2 : 1;
-        const int items = 128 * G.nkc;
-        for (int t = threadIdx.x; t < items * nplanes; t += kThreads) {
-            const int pl = t / items, it = t % items;
-            const int m = it / G.nkc, kc = it % G.nkc;
-            const int u = kc / G.pw, q = kc % G.pw;
-            const int mw = m >> 5, ml = m & 31;
-            const int ry = ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
-            const int rx = rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (ry < G.n_ry && rx < G.n_rx && u < G.p) {
-                const uint16_t* plane = pl ? P.plane1 : P.plane0;
-                const uint16_t* row = plane + (size_t)(ry * G.s + u) * G.plane_pitch;
-                val = load_shifted16(row, rx * G.s * G.Cp + 8 * q);
-                // zero the elements beyond the patch row (p * Cp elements)
-                const int valid = G.p * G.Cp - 8 * q;
-                if (valid < 8) {
-                    uint32_t w[4] = {val.x, val.y, val.z, val.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (2 * i >= valid) w[i] = 0;
-                        else if (2 * i + 1 >= valid) w[i] &= 0xffffu;
-                    }
-                    val = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-            }
-            if (!kF32) {
-                // uint8: A = 2 (x - 128), exact in bf16, so the MMA yields 2 <X_r, X_j>
-                uint32_t w[4] = {val.x, val.y, val.z, val.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
-                    const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
-                    w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
-                }
-                val = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-            uint8_t* base = smem + (pl ? G.off_a1 : G.off_a0);
-            *reinterpret_cast<uint4*>(base + (size_t)(m >> 3) * G.nkc * 128 + kc * 128 +
-                                      (m & 7) * 16) = val;
+    // A_norm (shared by all tiles): [group][2 kchunks][8 x 16 B], the
+    // coefficients of the norm pieces
+    for (int t = threadIdx.x; t < 128 * 2; t += kThreads) {
+        const int m = t >> 1, kc = t & 1;
+        uint16_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (kc == 0) {
+            const uint16_t cn = bf16_bits(kF32 ? -0.5f : -1.0f);
+            c[0] = c[1] = c[2] = cn;
+            if (kF32) c[3] = c[4] = c[5] = bf16_bits(kEps);
         }
-        // A_norm: [group][2 kchunks][8 x 16 B]; row = coefficients of the norm pieces
-        for (int t = threadIdx.x; t < 128 * 2; t += kThreads) {
-            const int m = t >> 1, kc = t & 1;
-            uint16_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (kc == 0) {
-                const uint16_t cn = bf16_bits(kF32 ? -0.5f : -1.0f);
-                c[0] = c[1] = c[2] = cn;
-                if (kF32) c[3] = c[4] = c[5] = bf16_bits(kEps);
-            }
-            uint4 val = make_uint4(c[0] | (uint32_t(c[1]) << 16), c[2] | (uint32_t(c[3]) << 16),
-                                   c[4] | (uint32_t(c[5]) << 16), c[6] | (uint32_t(c[7]) << 16));
-            *reinterpret_cast<uint4*>(smem + G.off_an + (m >> 3) * 256 + kc * 128 + (m & 7) * 16) = val;
-        }
+        const uint4 val = make_uint4(c[0] | (uint32_t(c[1]) << 16), c[2] | (uint32_t(c[3]) << 16),
+                                     c[4] | (uint32_t(c[5]) << 16), c[6] | (uint32_t(c[7]) << 16));
+        *reinterpret_cast<uint4*>(smem + G.off_an + (m >> 3) * 256 + kc * 128 + (m & 7) * 16) = val;
     }
     // stage buffers start zeroed so padding rows are finite
     for (int t = threadIdx.x; t < kStages * G.stage_bytes / 16; t += kThreads)
         reinterpret_cast<uint4*>(smem + G.off_stage)[t] = make_uint4(0, 0, 0, 0);
-    // epilogue threads: empty heaps
-    if (LC == 0 && threadIdx.x < 128) {
-        unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + G.off_heap) + threadIdx.x;
-        for (int i = 0; i < G.HL; ++i) h[i * 128] = kEmpty;
-    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -580,25 +592,95 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
     if (warp >= EW && warp < kMmaWarp) {
         // ------------------------------------------------------------ producers
         const int pt = threadIdx.x - kEpi;
-        const int nplanes = kF32 ? 2 : 1;
         const int strip_items = nplanes * G.pw * G.kcols * G.Rb;
         const int norm_items = G.kcols * G.Rb;
-        const int* nrm_i = static_cast<const int*>(P.nrm);
-        const float* nrm_f = static_cast<const float*>(P.nrm);
-        for (int c = 0; c < nchunks; ++c) {
-            const int stage = c % kStages, use = c / kStages;
+        TileInfo ti[NS];
+        int chunk[NS], turn[NS];
+        bool active[NS];
+        for (int k = 0; k < NS; ++k) {
+            turn[k] = 0;
+            chunk[k] = 0;
+            const int t = slot_tile(cta, 0, k, NS, grid);
+            active[k] = t < P.total_tiles;
+            if (active[k]) ti[k] = tile_info(P, t);
+        }
+        int step = 0, next = 0;
+        bool ok = true;
+        while (ok) {
+            int k = next;
+            if (!active[k]) k = NS - 1 - k;
+            if (!active[k]) break;
+            next = NS - 1 - k;
+            const TileInfo& T = ti[k];
+            const TcJob& J = *T.job;
+            if (chunk[k] == 0) {
+                // new tile for slot k: stage its A operand once the previous
+                // tile's MMAs are done with the region
+                if (turn[k] > 0 && !mbar_wait(bar_aempty + 8 * k, (turn[k] - 1) & 1, abort_flag, 5)) {
+                    ok = false;
+                    break;
+                }
+                const int items = 128 * G.nkc * nplanes;
+                for (int t0 = pt; t0 < items; t0 += 4 * kProducers) {
+                    uint4 val[4];
+                    int dst[4];
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4) {
+                        const int t = t0 + u4 * kProducers;
+                        dst[u4] = -1;
+                        val[u4] = make_uint4(0, 0, 0, 0);
+                        if (t >= items) continue;
+                        const int pl = t / (128 * G.nkc), it = t % (128 * G.nkc);
+                        const int m = it / G.nkc, kc = it % G.nkc;
+                        const int u = kc / G.pw, q = kc % G.pw;
+                        const int mw = m >> 5, ml = m & 31;
+                        const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
+                        const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
+                        dst[u4] = k * G.a_bytes * nplanes + pl * G.a_bytes +
+                                  (m >> 3) * G.nkc * 128 + kc * 128 + (m & 7) * 16;
+                        if (ry < J.n_ry && rx < J.n_rx && u < G.p) {
+                            const uint16_t* plane = pl ? J.plane1 : J.plane0;
+                            const uint16_t* row = plane + (size_t)(ry * G.s + u) * J.plane_pitch;
+                            uint4 v = load_shifted16(row, rx * G.s * G.Cp + 8 * q);
+                            // zero the elements beyond the patch row (p * Cp elements)
+                            const int valid = G.p * G.Cp - 8 * q;
+                            uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                if (2 * i >= valid) w[i] = 0;
+                                else if (2 * i + 1 >= valid) w[i] &= 0xffffu;
+                                if (!kF32) {
+                                    // uint8: A = 2 (x - 128), exact in bf16: MMA gives 2 <X_r, X_j>
+                                    const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
+                                    const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
+                                    w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
+                                }
+                            }
+                            val[u4] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4)
+                        if (dst[u4] >= 0)
+                            *reinterpret_cast<uint4*>(smem + G.off_a + dst[u4]) = val[u4];
+                }
+                fence_proxy_async();
+                mbar_arrive(bar_afull + 8 * k);
+            }
+            // one chunk of candidate columns of slot k's tile
+            const int stage = step % kStages, use = step / kStages;
             if (use > 0 && !mbar_wait(bar_empty + 8 * stage, (use - 1) & 1, abort_flag, 1)) break;
             uint8_t* sb = smem + G.off_stage + stage * G.stage_bytes;
-            const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
-            const int kc_here = min(G.kcols, NX - jc0);
+            const int jc0 = chunk_order(chunk[k], T.nchunks, T.center_chunk) * G.kcols;
+            const int kc_here = min(G.kcols, T.NX - jc0);
             for (int t0 = pt; t0 < strip_items; t0 += 4 * kProducers) {
                 uint4 val[4];
                 int dst[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int t = t0 + k * kProducers;
-                    dst[k] = -1;
-                    val[k] = make_uint4(0, 0, 0, 0);
+                for (int u4 = 0; u4 < 4; ++u4) {
+                    const int t = t0 + u4 * kProducers;
+                    dst[u4] = -1;
+                    val[u4] = make_uint4(0, 0, 0, 0);
                     if (t >= strip_items) continue;
                     int r = t;
                     const int row = r % G.Rb; r /= G.Rb;
@@ -606,24 +688,26 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     const int q = r % G.pw;
                     const int pl = r / G.pw;
                     if (jl >= kc_here) continue;
-                    dst[k] = pl * G.plane_stage + q * G.qpitch + (jl * G.Rb + row) * 16;
-                    if (row < NR + G.p_eff - 1) {  // rows past that feed no real candidate
-                        const uint16_t* plane = pl ? P.plane1 : P.plane0;
-                        const uint16_t* prow = plane + (size_t)(Y0 + row) * G.plane_pitch;
-                        val[k] = load_shifted16(prow, (X0 + jc0 + jl) * G.Cp + 8 * q);
+                    dst[u4] = pl * G.plane_stage + q * G.qpitch + (jl * G.Rb + row) * 16;
+                    if (row < T.NR + G.p_eff - 1) {  // rows past that feed no real candidate
+                        const uint16_t* plane = pl ? J.plane1 : J.plane0;
+                        const uint16_t* prow = plane + (size_t)(T.Y0 + row) * J.plane_pitch;
+                        val[u4] = load_shifted16(prow, (T.X0 + jc0 + jl) * G.Cp + 8 * q);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (dst[k] >= 0) *reinterpret_cast<uint4*>(sb + dst[k]) = val[k];
+                for (int u4 = 0; u4 < 4; ++u4)
+                    if (dst[u4] >= 0) *reinterpret_cast<uint4*>(sb + dst[u4]) = val[u4];
             }
             uint8_t* nsb = sb + nplanes * G.plane_stage;
+            const int* nrm_i = static_cast<const int*>(J.nrm);
+            const float* nrm_f = static_cast<const float*>(J.nrm);
             for (int t = pt; t < norm_items; t += kProducers) {
                 const int row = t % G.Rb, jl = t / G.Rb;
                 if (jl >= kc_here) continue;
                 uint16_t hi = 0, mid = 0, lo = 0;
-                if (row < NR) {
-                    const size_t ni = (size_t)(Y0 + row) * G.Wc + (X0 + jc0 + jl);
+                if (row < T.NR) {
+                    const size_t ni = (size_t)(T.Y0 + row) * J.Wc + (T.X0 + jc0 + jl);
                     const float w = kF32 ? nrm_f[ni] : (float)nrm_i[ni];
                     split3(w, hi, mid, lo);
                 } else {
@@ -640,37 +724,65 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             }
             fence_proxy_async();
             mbar_arrive(bar_full + 8 * stage);
+            ++step;
+            if (++chunk[k] == T.nchunks) {
+                chunk[k] = 0;
+                ++turn[k];
+                const int t = slot_tile(cta, turn[k], k, NS, grid);
+                active[k] = t < P.total_tiles;
+                if (active[k]) ti[k] = tile_info(P, t);
+            }
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t a0 = smem_u32(smem + G.off_a0), a1 = smem_u32(smem + G.off_a1);
             const uint32_t an = smem_u32(smem + G.off_an);
             const uint32_t sbo_a = G.nkc * 128;
-            const int nplanes = kF32 ? 2 : 1;
             const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
-            int c = 0;
-            for (; c < nchunks; ++c) {
-                const int stage = c % kStages, use = c / kStages;
-                const int buf = c & 1, ub = c >> 1;
-                if (ub > 0 && !mbar_wait(bar_tempty + 8 * buf, (ub - 1) & 1, abort_flag, 2)) break;
+            int nchunks[NS], center[NS], NX[NS], chunk[NS], turn[NS], q[NS];
+            bool active[NS];
+            for (int k = 0; k < NS; ++k) {
+                chunk[k] = turn[k] = q[k] = 0;
+                const int t = slot_tile(cta, 0, k, NS, grid);
+                active[k] = t < P.total_tiles;
+                if (active[k]) {
+                    const TileInfo T = tile_info(P, t);
+                    nchunks[k] = T.nchunks; center[k] = T.center_chunk; NX[k] = T.NX;
+                }
+            }
+            int step = 0, next = 0;
+            while (true) {
+                int k = next;
+                if (!active[k]) k = NS - 1 - k;
+                if (!active[k]) break;
+                next = NS - 1 - k;
+                if (chunk[k] == 0 &&
+                    !mbar_wait(bar_afull + 8 * k, turn[k] & 1, abort_flag, 6))
+                    break;
+                const int buf = q[k] & 1, ub = q[k] >> 1;
+                if (ub > 0 &&
+                    !mbar_wait(bar_tempty + 8 * (2 * k + buf), (ub - 1) & 1, abort_flag, 2))
+                    break;
+                const int stage = step % kStages, use = step / kStages;
                 if (!mbar_wait(bar_full + 8 * stage, use & 1, abort_flag, 3)) break;
                 tc_fence_after();
-                const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
-                const int kc_here = min(G.kcols, NX - jc0);
+                const int jc0 = chunk_order(chunk[k], nchunks[k], center[k]) * G.kcols;
+                const int kc_here = min(G.kcols, NX[k] - jc0);
                 const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
-                const uint32_t d = tmem_base + buf * kBufCols;
+                const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
                 const uint32_t sb = smem_u32(smem + G.off_stage + stage * G.stage_bytes);
+                const uint32_t a0 = smem_u32(smem + G.off_a + k * G.a_bytes * nplanes);
+                const uint32_t a1 = a0 + G.a_bytes;
                 uint32_t acc = 0;
                 for (int t = 0; t < G.nkc / 2; ++t) {
                     const int kc = 2 * t;
-                    const int u = kc / G.pw, q = kc % G.pw;
-                    const uint32_t boff = q * G.qpitch + u * 16;
+                    const int u = kc / G.pw, qq = kc % G.pw;
+                    const uint32_t boff = qq * G.qpitch + u * 16;
                     const uint64_t da0 = sdesc(a0 + kc * 128, 128, sbo_a);
                     const uint64_t db0 = sdesc(sb + boff, lbo_b, 128);
                     mma_bf16(d, da0, db0, idesc, acc);
                     acc = 1;
-                    if (nplanes == 2) {
+                    if (kF32) {
                         const uint64_t db1 = sdesc(sb + G.plane_stage + boff, lbo_b, 128);
                         const uint64_t da1 = sdesc(a1 + kc * 128, 128, sbo_a);
                         mma_bf16(d, da0, db1, idesc, 1);
@@ -680,7 +792,20 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 const uint32_t nsb = sb + nplanes * G.plane_stage;
                 mma_bf16(d, sdesc(an, 128, 256), sdesc(nsb, 16, 128), idesc, 1);
                 mma_commit(bar_empty + 8 * stage);
-                mma_commit(bar_tfull + 8 * buf);
+                mma_commit(bar_tfull + 8 * (2 * k + buf));
+                ++step;
+                ++q[k];
+                if (++chunk[k] == nchunks[k]) {
+                    mma_commit(bar_aempty + 8 * k);  // A region of slot k free once these finish
+                    chunk[k] = 0;
+                    ++turn[k];
+                    const int t = slot_tile(cta, turn[k], k, NS, grid);
+                    active[k] = t < P.total_tiles;
+                    if (active[k]) {
+                        const TileInfo T = tile_info(P, t);
+                        nchunks[k] = T.nchunks; center[k] = T.center_chunk; NX[k] = T.NX;
+                    }
+                }
             }
             // drain: wait for every MMA issued by this thread before TMEM is freed
             mma_commit(bar_done);
@@ -691,48 +816,57 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        // Per lane: a max-heap of the best keys (uint8: (d, offset), float32:
-        // (-v, offset)) and an append buffer.  Values at or above the lane's
-        // threshold are appended with predicated stores (no divergent work);
-        // when any lane's buffer nears full the whole warp merges its buffers
-        // into the heaps in lock-step.
-        const int quarter = warp & 3, half = warp >> 2;
+        // Slot k = warp / 4.  Per lane: the best keys of its reference (uint8:
+        // (d, offset), float32: (-v, offset)) in a register list (or a shared-
+        // memory heap for large K) behind an append buffer: values at or above
+        // the lane's threshold are appended with predicated stores; when any
+        // lane's buffer nears full the warp merges in lock-step.
+        const int k = warp >> 2, quarter = warp & 3;
+        unsigned long long* pend =
+            reinterpret_cast<unsigned long long*>(smem + G.off_buf) + threadIdx.x;
         Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + (threadIdx.x & 127), G.HL};
-        RegTopK<LC == 0 ? 1 : LC> reg;
-        reg.init(G.HL);
-        unsigned long long* pend = reinterpret_cast<unsigned long long*>(smem + G.off_buf) + threadIdx.x;
-        const int ry = ry0 + (quarter / G.wgx) * G.rr + lane / G.rc;
-        const int rx = rx0 + (quarter % G.wgx) * G.rc + lane % G.rc;
-        const bool lane_ok = ry < G.n_ry && rx < G.n_rx;
-        const int yr = ry * G.s, xr = rx * G.s;
-        // this lane's candidate rows inside the strip (empty if the lane has no reference)
-        const int lo = lane_ok ? max(0, yr - G.h - Y0) : 1 << 20;
-        const int hi = lane_ok ? min(NR - 1, yr + G.h - Y0) : -1;
-        const int* nrm_i = static_cast<const int*>(P.nrm);
-        const int nr_i = (lane_ok && !kF32) ? nrm_i[(size_t)yr * G.Wc + xr] : 0;
-        float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
-        int cnt = 0;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1, ub = c >> 1;
-            if (!mbar_wait(bar_tfull + 8 * buf, ub & 1, abort_flag, 4)) break;
-            tc_fence_after();
-            const int jc0 = chunk_order(c, nchunks, center_chunk) * G.kcols;
-            const int kc_here = min(G.kcols, NX - jc0);
-            for (int jl = 0; jl < kc_here; ++jl) {
-                if (EW == 8 && ((c * G.kcols + jl) & 1) != half) continue;  // partner's column
-                const int xc = X0 + jc0 + jl;
-                const bool xok = lane_ok && abs(xc - xr) <= G.h;
-                if (!__any_sync(0xffffffffu, xok)) continue;
-                // rows any lane of the warp needs in this column (warp-uniform)
-                const int wlo = __reduce_min_sync(0xffffffffu, xok ? lo : 1 << 20);
-                const int whi = __reduce_max_sync(0xffffffffu, xok ? hi : -1);
-                const int b0 = wlo >> 4, nblk = (whi >> 4) - b0 + 1;
-                const uint32_t colbase = tmem_base + lane_base + buf * kBufCols + jl * G.Rb + 16 * b0;
-                for (int bb = 0; bb < nblk; ++bb) {
-                    float w[16];
-                    tmem_ld_blocks<1>(colbase + 16 * bb, w);
-                    {
+        int qc = 0;  // slot-local chunk counter (TMEM buffer phase)
+        for (int turn = 0; !*abort_flag; ++turn) {
+            const int tile = slot_tile(cta, turn, k, NS, grid);
+            if (tile >= P.total_tiles) break;
+            const TileInfo T = tile_info(P, tile);
+            const TcJob& J = *T.job;
+            RegTopK<LC == 0 ? 1 : LC> reg;
+            reg.init(G.HL);
+            if constexpr (LC == 0) {
+                for (int i = 0; i < G.HL; ++i) heap.h[i * 128] = kEmpty;
+            }
+            const int ry = T.ry0 + (quarter / G.wgx) * G.rr + lane / G.rc;
+            const int rx = T.rx0 + (quarter % G.wgx) * G.rc + lane % G.rc;
+            const bool lane_ok = ry < J.n_ry && rx < J.n_rx;
+            const int yr = ry * G.s, xr = rx * G.s;
+            // this lane's candidate rows inside the strip (empty if no reference)
+            const int lo = lane_ok ? max(0, yr - G.h - T.Y0) : 1 << 20;
+            const int hi = lane_ok ? min(T.NR - 1, yr + G.h - T.Y0) : -1;
+            const int* nrm_i = static_cast<const int*>(J.nrm);
+            const int nr_i = (lane_ok && !kF32) ? nrm_i[(size_t)yr * J.Wc + xr] : 0;
+            float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
+            int cnt = 0;
+            for (int c = 0; c < T.nchunks; ++c, ++qc) {
+                const int buf = qc & 1, ub = qc >> 1;
+                if (!mbar_wait(bar_tfull + 8 * (2 * k + buf), ub & 1, abort_flag, 4)) break;
+                tc_fence_after();
+                const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                const int kc_here = min(G.kcols, T.NX - jc0);
+                for (int jl = 0; jl < kc_here; ++jl) {
+                    const int xc = T.X0 + jc0 + jl;
+                    const bool xok = lane_ok && abs(xc - xr) <= G.h;
+                    if (!__any_sync(0xffffffffu, xok)) continue;
+                    // rows any lane of the warp needs in this column (warp-uniform)
+                    const int wlo = __reduce_min_sync(0xffffffffu, xok ? lo : 1 << 20);
+                    const int whi = __reduce_max_sync(0xffffffffu, xok ? hi : -1);
+                    const int b0 = wlo >> 4, nblk = (whi >> 4) - b0 + 1;
+                    const uint32_t colbase = tmem_base + lane_base + (2 * k + buf) * G.bufcols +
+                                             jl * G.Rb + 16 * b0;
+                    for (int bb = 0; bb < nblk; ++bb) {
+                        float w[16];
+                        tmem_ld_blocks<1>(colbase + 16 * bb, w);
                         const int b = b0 + bb;
                         // this lane's valid rows of block b: [i0, i1] (may be empty)
                         const int i0 = lo - 16 * b, i1 = xok ? hi - 16 * b : -1;
@@ -747,13 +881,13 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                         const bool hit = m >= thr;
                         if (!__any_sync(0xffffffffu, hit)) continue;  // next block
                         if (hit) {
-                            const int ybase = Y0 + 16 * b;
+                            const int ybase = T.Y0 + 16 * b;
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
                                 if (i >= i0 && i <= i1 && w[i] >= thr) {
                                     pend[cnt * kEpi] =
                                         ((unsigned long long)__float_as_uint(w[i]) << 32) |
-                                        (unsigned)((ybase + i) * G.W + xc);
+                                        (unsigned)((ybase + i) * J.W + xc);
                                     ++cnt;
                                 }
                             }
@@ -763,54 +897,38 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                             merge_pending<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(bar_tempty + 8 * (2 * k + buf));
             }
-            tc_fence_before();
-            mbar_arrive(bar_tempty + 8 * buf);
-        }
-        if (__any_sync(0xffffffffu, cnt > 0))
-            reg = final_merge<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
-        if constexpr (EW == 8 && LC > 0) {
-            // combine the two half-lists of each lane quarter: warps 4-7 hand
-            // their keys to warps 0-3 through the pending buffers
-            asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
-            if (half == 1) {
+            if (__any_sync(0xffffffffu, cnt > 0))
+                reg = final_merge<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
+            // ---- write results
+            if (lane_ok && !*abort_flag) {
+                const size_t ref = (size_t)ry * J.n_rx + rx;
+                if constexpr (LC == 0 && !kF32) heap.sort();
+                const int nout = kF32 ? G.HL : G.K;
+                auto emit = [&](int i, unsigned long long key) {
+                    if (kF32) {
+                        // pool: any order; the re-rank kernel ranks it
+                        J.pool_idx[ref * G.HL + i] =
+                            key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
+                        J.pool_score[ref * G.HL + i] =
+                            key == kEmpty ? -__int_as_float(0x7f800000)
+                                          : from_orderable(~(unsigned)(key >> 32));
+                    } else {
+                        J.out_idx[ref * G.K + i] =
+                            key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
+                        J.out_dist[ref * G.K + i] =
+                            key == kEmpty ? 0x7fffffff : (int32_t)(unsigned)(key >> 32);
+                    }
+                };
+                if constexpr (LC > 0) {
 #pragma unroll
-                for (int i = 0; i < LC; ++i) pend[i * kEpi] = reg.a[i];
-            }
-            asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
-            if (half == 0) {
-                const unsigned long long* other = pend + 128;
-#pragma unroll 1
-                for (int j0 = 0; j0 < LC; j0 += kBatch) {
-                    unsigned long long b[kBatch];
-#pragma unroll
-                    for (int t = 0; t < kBatch; ++t) b[t] = other[(j0 + t) * kEpi];
-                    reg.merge_batch(b);
-                }
-            }
-        }
-        // ---- write results
-        if (half == 0 && lane_ok && !*abort_flag) {
-            const size_t ref = (size_t)ry * G.n_rx + rx;
-            if constexpr (LC == 0 && !kF32) heap.sort();
-            const int nout = kF32 ? G.HL : G.K;
-            auto emit = [&](int k, unsigned long long key) {
-                if (kF32) {
-                    // pool: any order; the re-rank kernel ranks it
-                    P.pool_idx[ref * G.HL + k] = key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
-                    P.pool_score[ref * G.HL + k] = key == kEmpty ? -__int_as_float(0x7f800000)
-                                                                : from_orderable(~(unsigned)(key >> 32));
+                    for (int i = 0; i < LC; ++i)
+                        if (i < nout) emit(i, reg.a[i]);
                 } else {
-                    P.out_idx[ref * G.K + k] = key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
-                    P.out_dist[ref * G.K + k] = key == kEmpty ? 0x7fffffff : (int32_t)(unsigned)(key >> 32);
+                    for (int i = 0; i < nout; ++i) emit(i, heap.h[i * 128]);
                 }
-            };
-            if constexpr (LC > 0) {
-#pragma unroll
-                for (int i = 0; i < LC; ++i)
-                    if (i < nout) emit(i, reg.a[i]);
-            } else {
-                for (int k = 0; k < nout; ++k) emit(k, heap.h[k * 128]);
             }
         }
     }
@@ -824,33 +942,42 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
     if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, 0x100 + *abort_flag);
 }
 
+// Class geometry for a job shape: lane mapping, strips, slots, shared memory.
 bool make_tc_geom(const Geom& g, TcGeom& t) {
-    t.H = g.H; t.W = g.W; t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
-    t.n_ry = g.n_ry; t.n_rx = g.n_rx; t.Hc = g.Hc; t.Wc = g.Wc;
+    t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
     t.pw = g.pw; t.p_eff = g.p_eff; t.nkc = g.p_eff * g.pw;
     t.f32 = g.dtype == kF32;
     t.HL = t.f32 ? g.L : g.K;
-    t.plane_pitch = g.plane_pitch;
-    // lane -> reference mapping: rr reference rows x rc columns per warp, a
-    // wgy x wgx grid of 4 warps; pick the one with the least MMA work
-    // (union columns x strip rows), preferring narrow warps (rc small) on ties.
-    static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
-    long long best = -1;
-    for (const auto& mp : kMaps) {
-        const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
-        const int ty = wgy * rr, tx = wgx * rc;
-        const int nr_max = (ty - 1) * g.s + 2 * g.h + 1;
-        const int nx_max = (tx - 1) * g.s + 2 * g.h + 1;
-        const int rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
-        if (rb > kBufCols) continue;
-        const long long work = (long long)nx_max * rb;
-        if (best < 0 || work < best) {
-            best = work;
-            t.rr = rr; t.rc = rc; t.wgx = wgx; t.ty = ty; t.tx = tx; t.Rb = rb;
+    // two tiles in flight when the list lives in registers and a strip fits
+    // a 128-column accumulator; one otherwise
+    for (int ns = 2; ns >= 1; --ns) {
+        if (ns == 2 && t.HL > 32) continue;
+        const int bufcols = kTmemCols / (2 * ns);
+        // lane -> reference mapping: rr reference rows x rc columns per warp,
+        // a wgy x wgx grid of 4 warps; least MMA work (union columns x strip
+        // rows), ties to the earlier (narrower) entry
+        static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
+        long long best = -1;
+        for (const auto& mp : kMaps) {
+            const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
+            const int ty = wgy * rr, tx = wgx * rc;
+            const int nr_max = (ty - 1) * g.s + 2 * g.h + 1;
+            const int nx_max = (tx - 1) * g.s + 2 * g.h + 1;
+            const int rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
+            if (rb > bufcols) continue;
+            const long long work = (long long)nx_max * rb;
+            if (best < 0 || work < best) {
+                best = work;
+                t.rr = rr; t.rc = rc; t.wgx = wgx; t.ty = ty; t.tx = tx; t.Rb = rb;
+            }
         }
+        if (best < 0) continue;
+        t.nslots = ns;
+        t.bufcols = bufcols;
+        break;
     }
-    if (best < 0) return false;
-    t.kcols = kBufCols / t.Rb;
+    if (t.Rb <= 0 || t.Rb > kBufCols) return false;
+    t.kcols = t.bufcols / t.Rb;
     const int strip_rows = t.kcols * t.Rb + g.p_eff + 16;
     t.qpitch = strip_rows * 16;
     t.plane_stage = t.pw * t.qpitch;
@@ -858,54 +985,105 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
     const int nplanes = t.f32 ? 2 : 1;
     t.stage_bytes = (nplanes * t.plane_stage + t.ns_bytes + 127) / 128 * 128;
     int off = 0;
-    const int a_bytes = 128 * t.nkc * 16;
-    t.off_a0 = off; off += a_bytes;
-    t.off_a1 = off; off += t.f32 ? a_bytes : 0;
+    t.a_bytes = 128 * t.nkc * 16;
+    t.off_a = off; off += t.nslots * nplanes * t.a_bytes;
     t.off_an = off; off += 128 * 2 * 16;
     t.off_stage = off; off += kStages * t.stage_bytes;
-    const int ew = t.HL <= 32 ? 8 : 4;  // epilogue warps (the shared-memory heap keeps 4)
     t.off_heap = off; off += t.HL > 32 ? 128 * t.HL * 8 : 0;
-    t.off_buf = off; off += ew * 32 * kBuf * 8;
-    t.off_bar = off; off += (2 * kStages + 5) * 8 + 16;
+    t.off_buf = off; off += 4 * t.nslots * 32 * kBuf * 8;
+    t.off_bar = off; off += (2 * kStages + 6 * t.nslots + 1) * 8 + 16;
     t.smem_total = (off + 1023) / 1024 * 1024;
-    // the plane padding covers the widest read (see make_geom)
     return t.smem_total <= kSmemLimit;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+TcJob make_job(const Geom& g, const TcGeom& t, const TcArgs& a, int tile_begin) {
+    TcJob j{};
+    j.plane0 = a.plane0;
+    j.plane1 = a.plane1;
+    j.nrm = a.nrm;
+    j.out_idx = a.out_idx;
+    j.out_dist = a.out_dist;
+    j.pool_idx = a.pool_idx;
+    j.pool_score = a.pool_score;
+    j.H = g.H; j.W = g.W; j.n_ry = g.n_ry; j.n_rx = g.n_rx; j.Hc = g.Hc; j.Wc = g.Wc;
+    j.plane_pitch = g.plane_pitch;
+    j.tiles_x = (g.n_rx + t.tx - 1) / t.tx;
+    j.tile_begin = tile_begin;
+    return j;
+}
+
+cudaError_t launch_params(TcParams& P, cudaStream_t st) {
+    const TcGeom& T = P.g;
+    const int smem = T.smem_total < 116 * 1024 ? 116 * 1024 : T.smem_total;
+    void (*kern)(TcParams);
+    int threads;
+    if (T.nslots == 2) {
+        threads = cta_threads<8>();
+        if (T.f32) kern = tc_match_kernel<32, true, 2>;
+        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 2> : tc_match_kernel<32, false, 2>;
+    } else {
+        threads = cta_threads<4>();
+        if (T.f32) kern = T.HL <= 32 ? tc_match_kernel<32, true, 1> : tc_match_kernel<0, true, 1>;
+        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 1>
+                  : T.HL <= 32 ? tc_match_kernel<32, false, 1> : tc_match_kernel<0, false, 1>;
+    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int per = T.nslots;
+    int grid = (P.total_tiles + per - 1) / per;
+    if (grid > num_sms()) grid = num_sms();
+    if (grid < 1) grid = 1;
+    kern<<<grid, threads, smem, st>>>(P);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_supported(const Geom& g) {
-    TcGeom t;
+    TcGeom t{};
     return make_tc_geom(g, t);
 }
 
+// Jobs that can share one persistent launch (same class geometry).
+bool tc_same_class(const Geom& a, const Geom& b) {
+    return a.dtype == b.dtype && a.Cp == b.Cp && a.p == b.p && a.h == b.h && a.s == b.s &&
+           a.K == b.K && a.L == b.L;
+}
+
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {
-    TcParams P{};
-    if (!make_tc_geom(g, P.g)) return cudaErrorNotSupported;
-    P.plane0 = a.plane0;
-    P.plane1 = a.plane1;
-    P.nrm = a.nrm;
-    P.out_idx = a.out_idx;
-    P.out_dist = a.out_dist;
-    P.pool_idx = a.pool_idx;
-    P.pool_score = a.pool_score;
-    P.status = a.status;
-    // at least 114 KB of shared memory keeps one CTA per SM (whole-TMEM allocation)
-    const int smem = P.g.smem_total < 116 * 1024 ? 116 * 1024 : P.g.smem_total;
-    dim3 grid((g.n_rx + P.g.tx - 1) / P.g.tx, (g.n_ry + P.g.ty - 1) / P.g.ty);
-    void (*kern)(TcParams);
-    int threads;
-    if (P.g.HL <= 32) {
-        threads = cta_threads<8>();
-        if (P.g.f32) kern = tc_match_kernel<32, true, 8>;
-        else kern = P.g.HL <= 16 ? tc_match_kernel<16, false, 8> : tc_match_kernel<32, false, 8>;
-    } else {
-        threads = cta_threads<4>();
-        kern = P.g.f32 ? tc_match_kernel<0, true, 4> : tc_match_kernel<0, false, 4>;
+    return launch_tc_batch(&g, &a, 1, st);
+}
+
+cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st) {
+    int i = 0;
+    while (i < n) {
+        static thread_local TcParams P;
+        P = TcParams{};
+        if (!make_tc_geom(gs[i], P.g)) return cudaErrorNotSupported;
+        P.status = as[i].status;
+        int tiles = 0, nj = 0;
+        while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj])) {
+            P.jobs[nj] = make_job(gs[i], P.g, as[i], tiles);
+            tiles += P.jobs[nj].tiles_x * ((gs[i].n_ry + P.g.ty - 1) / P.g.ty);
+            ++nj;
+            ++i;
+        }
+        P.njobs = nj;
+        P.total_tiles = tiles;
+        cudaError_t e = launch_params(P, st);
+        if (e != cudaSuccess) return e;
     }
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<grid, threads, smem, st>>>(P);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace bm
