@@ -70,7 +70,8 @@ typedef enum {
     BM_ERR_CUDA = -4,        /* a CUDA call failed; see bm_last_error     */
     BM_ERR_TIMEOUT = -5,     /* a bounded device wait ran out             */
     BM_ERR_BUSY = -6,        /* request alone exceeds the budget          */
-    BM_ERR_NOT_FOUND = -7    /* unknown ticket                            */
+    BM_ERR_NOT_FOUND = -7,   /* unknown ticket                            */
+    BM_ERR_TOO_LARGE = -8    /* job exceeds bm_match_static's scratch     */
 } bm_status;
 
 /* Algorithm selector for bm_set_algo. */
@@ -200,6 +201,49 @@ typedef struct {
  */
 int bm_set_timing(bm_ctx* ctx, int enable);
 int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset);
+
+/*
+ * bm_match_static -- bm_match without any allocation.
+ *
+ * The paper has no counterpart: this entry point serves callers that must
+ * not allocate device memory while they run.  cudaMalloc and cudaFree
+ * synchronise the whole device, which stalls a latency-bound loop, and in a
+ * process whose device memory is already held by another allocator (a
+ * framework's caching allocator, a fixed arena) a fresh allocation can fail
+ * part-way through a run.  bm_match_static needs no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine: every intermediate
+ * buffer (bf16 operand planes, patch norms, float32 candidate pool, status
+ * word, counters) is carved from one array in device memory of
+ * BM_STATIC_SCRATCH_BYTES (16 MiB), reserved with the library's module.
+ *
+ * Same arguments, conventions, validation and results as bm_match with the
+ * default algorithm (device pointers; asynchronous on `stream`).  A job
+ * whose working set (bm_static_scratch_bytes) exceeds the array returns
+ * BM_ERR_TOO_LARGE with nothing launched; bm_last_error(NULL) says how many
+ * bytes it needed.  For reference, a 512 x 512 float32 image with patch 8,
+ * stride 3, window 39, K 16 needs about 9.5 MB.
+ *
+ * Set-up: the first call on a device (the current device) looks up the
+ * array's address there with cudaGetSymbolAddress.  Make that first call
+ * before any stream capture begins.
+ *
+ * Sharing: every call on a device uses the same array.  Each call first
+ * clears the part that must start at zero (status word and counters) on
+ * `stream`; everything else is overwritten before it is read.  Calls whose
+ * work overlaps on the GPU (different streams with no ordering between
+ * them, or calls from several threads) race on the array and give wrong
+ * results: order them on one stream, or with events.
+ */
+#define BM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Scratch bytes bm_match_static needs for this job (0 if the arguments are
+ * invalid or unsupported).  Host only. */
+size_t bm_static_scratch_bytes(int H, int W, int C, bm_dtype dtype,
+                               int patch, int window, int stride, int K);
+
+int bm_match_static(const void* img, int H, int W, int C, bm_dtype dtype,
+                    int patch, int window, int stride, int K,
+                    int32_t* out_idx, void* out_dist, bm_stream stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,8 @@ from . import build_ext
 BM_U8, BM_F32 = 0, 1
 BM_OK = 0
 BM_ERR_INVALID, BM_ERR_UNSUPPORTED, BM_ERR_OOM, BM_ERR_CUDA = -1, -2, -3, -4
-BM_ERR_TIMEOUT, BM_ERR_BUSY, BM_ERR_NOT_FOUND = -5, -6, -7
+BM_ERR_TIMEOUT, BM_ERR_BUSY, BM_ERR_NOT_FOUND, BM_ERR_TOO_LARGE = -5, -6, -7, -8
+BM_STATIC_SCRATCH_BYTES = 16 << 20
 BM_ALGO_AUTO, BM_ALGO_SELFCONV_TC, BM_ALGO_DIRECT = 0, 1, 2
 
 INT32_MAX = 2**31 - 1
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = True):
             "bm_get_stats": ([vp, ctypes.POINTER(bm_stats)], ci),
             "bm_set_timing": ([vp, ci], ci),
             "bm_get_timing": ([vp, ctypes.POINTER(bm_timing), ci], ci),
+            "bm_static_scratch_bytes": ([ci, ci, ci, ci, ci, ci, ci, ci], sz),
+            "bm_match_static": ([vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -130,6 +133,17 @@ def bm_match(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_di
 def bm_match_direct(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist,
                     stream) -> int:
     return load().bm_match_direct(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx,
+                                  out_dist, stream)
+
+
+def bm_static_scratch_bytes(H, W, C, dtype, patch, window, stride, K) -> int:
+    return load().bm_static_scratch_bytes(H, W, C, dtype, patch, window, stride, K)
+
+
+def bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist,
+                    stream) -> int:
+    """No-allocation matcher (fixed device scratch shared by all calls; see bm.h)."""
+    return load().bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx,
                                   out_dist, stream)
 
 

@@ -64,6 +64,19 @@ namespace {
 
 thread_local std::string t_last_error;
 
+}  // namespace
+
+namespace bm {
+// Sets the calling thread's bm_last_error message; for entry points defined
+// in other files of the library.
+int set_error(int code, const char* msg) {
+    t_last_error = msg;
+    return code;
+}
+}  // namespace bm
+
+namespace {
+
 struct Workspace {
     void* ptr = nullptr;
     size_t bytes = 0;

@@ -89,4 +89,7 @@ cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
                           int32_t* out_idx, float* out_dist, unsigned long long* counters,
                           cudaStream_t st);
 
+// Sets the calling thread's bm_last_error message and returns code.
+int set_error(int code, const char* msg);
+
 }  // namespace bm

@@ -18,7 +18,7 @@ def declared_functions():
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        for m in re.finditer(r"\b(?:int|void|const char\s*\*)\s+(bm_\w+)\s*\(", src):
+        for m in re.finditer(r"\b(?:int|void|size_t|const char\s*\*)\s+(bm_\w+)\s*\(", src):
             names.add(m.group(1))
     return sorted(names)
 
