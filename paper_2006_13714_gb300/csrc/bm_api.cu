@@ -17,6 +17,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -53,6 +54,7 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
 size_t plane_bytes(const Geom& g) { return (size_t)g.plane_rows * g.plane_pitch * 2; }
 size_t nrm_bytes(const Geom& g) { return (size_t)g.Hc * g.Wc * 4; }
 size_t pool_bytes(const Geom& g) { return g.dtype == kF32 ? (size_t)g.nR * g.L * 8 : 0; }
+size_t nsp_bytes(const Geom& g) { return (size_t)g.Hc * g.Wc * 16; }
 
 bool tc_supported(const Geom& g);  // selfconv_tc.cu
 
@@ -97,7 +99,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Byte layout of one tensor-core job's workspace.
 struct WsLayout {
-    size_t plane0, plane1, nrm, pool_idx, pool_score, status, total;
+    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, status, total;
 };
 
 WsLayout ws_layout(const Geom& g) {
@@ -106,6 +108,7 @@ WsLayout ws_layout(const Geom& g) {
     l.plane0 = off; off += align256(plane_bytes(g));
     l.plane1 = off; off += g.dtype == kF32 ? align256(plane_bytes(g)) : 0;
     l.nrm = off; off += align256(nrm_bytes(g));
+    l.nsp = off; off += align256(nsp_bytes(g));
     l.pool_idx = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
     l.pool_score = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
     l.status = off; off += 256;
@@ -128,7 +131,7 @@ struct bm_ctx {
     // stage timing
     std::atomic<int> timing{0};
     std::mutex tm_mu;
-    struct EvPair { int stage; cudaEvent_t a, b; };
+    struct EvPair { int stage; int n; cudaEvent_t a, b; };
     std::vector<EvPair> tm_pending;
     bm_timing tm_total{};
     // host-buffer path
@@ -187,8 +190,9 @@ size_t job_ws_bytes(bm_ctx* ctx, const Geom& g) {
 }
 
 // Run `launch` on st; with stage timing on, bracket it with two events.
+// nlaunch (optional) = kernel launches the bracket holds, read after launch().
 template <class F>
-cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch) {
+cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch, const int* nlaunch = nullptr) {
     if (!ctx->timing.load()) return launch();
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -197,24 +201,22 @@ cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch) {
     cudaError_t e = launch();
     cudaEventRecord(b, st);
     std::lock_guard<std::mutex> lk(ctx->tm_mu);
-    ctx->tm_pending.push_back({stage, a, b});
+    ctx->tm_pending.push_back({stage, nlaunch ? *nlaunch : 1, a, b});
     return e;
 }
 
-// Enqueue the kernels of one job on st, using workspace ws (size job_ws_bytes).
-int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st) {
+// First kernels of a tensor-core job on st (workspace ws of job_ws_bytes):
+// status reset, centring offset, bf16 planes, box filter; fills the
+// tensor-core arguments a.
+int prep_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st,
+             TcArgs& a) {
     cudaError_t e;
-    if (!use_tc(ctx, g)) {
-        e = timed(ctx, BM_STAGE_DIRECT, st,
-                  [&] { return launch_direct(g, r.img, r.out_idx, r.out_dist, st); });
-        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
-        return BM_OK;
-    }
     WsLayout l = ws_layout(g);
     char* b = static_cast<char*>(ws);
     uint16_t* p0 = reinterpret_cast<uint16_t*>(b + l.plane0);
     uint16_t* p1 = g.dtype == kF32 ? reinterpret_cast<uint16_t*>(b + l.plane1) : nullptr;
     void* nrm = b + l.nrm;
+    uint16_t* nsp = reinterpret_cast<uint16_t*>(b + l.nsp);
     int* status = reinterpret_cast<int*>(b + l.status);
     float* center = reinterpret_cast<float*>(b + l.status + 16);
     if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess)
@@ -226,12 +228,13 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
                    [&] { return launch_planes(g, r.img, center, p0, p1, st); })) != cudaSuccess)
         return cuda_fail(e, "plane kernel launch");
     if ((e = timed(ctx, BM_STAGE_BOX, st,
-                   [&] { return launch_boxfilter(g, r.img, center, nrm, st); })) != cudaSuccess)
+                   [&] { return launch_boxfilter(g, r.img, center, nrm, nsp, st); })) != cudaSuccess)
         return cuda_fail(e, "box filter launch");
-    TcArgs a{};
+    a = TcArgs{};
     a.plane0 = p0;
     a.plane1 = p1;
     a.nrm = nrm;
+    a.nsp = nsp;
     a.status = status;
     if (g.dtype == kU8) {
         a.out_idx = r.out_idx;
@@ -240,18 +243,37 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
         a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
         a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
     }
+    return BM_OK;
+}
+
+// Last kernel of a float32 tensor-core job: the boundary re-rank.
+int finish_job(bm_ctx* ctx, const Geom& g, const bm_request& r, const TcArgs& a, cudaStream_t st) {
+    if (g.dtype != kF32) return BM_OK;
+    cudaError_t e = timed(ctx, BM_STAGE_RERANK, st, [&] {
+        return launch_rerank(g, static_cast<const float*>(r.img), static_cast<const float*>(a.nrm),
+                             a.pool_idx, a.pool_score, r.out_idx, static_cast<float*>(r.out_dist),
+                             ctx->d_counters, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
+    return BM_OK;
+}
+
+// Enqueue the kernels of one job on st, using workspace ws (size job_ws_bytes).
+int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st) {
+    cudaError_t e;
+    if (!use_tc(ctx, g)) {
+        e = timed(ctx, BM_STAGE_DIRECT, st,
+                  [&] { return launch_direct(g, r.img, r.out_idx, r.out_dist, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+        return BM_OK;
+    }
+    TcArgs a;
+    int rc = prep_job(ctx, g, r, ws, st, a);
+    if (rc != BM_OK) return rc;
     if ((e = timed(ctx, BM_STAGE_TC, st, [&] { return launch_tc(g, a, st); })) != cudaSuccess)
         return cuda_fail(e, "tensor-core kernel launch");
     ctx->tc_jobs += 1;
-    if (g.dtype == kF32) {
-        e = timed(ctx, BM_STAGE_RERANK, st, [&] {
-            return launch_rerank(g, static_cast<const float*>(r.img), static_cast<const float*>(nrm),
-                                 a.pool_idx, a.pool_score, r.out_idx,
-                                 static_cast<float*>(r.out_dist), ctx->d_counters, st);
-        });
-        if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
-    }
-    return BM_OK;
+    return finish_job(ctx, g, r, a, st);
 }
 
 // Per-stream workspace of at least `bytes`, grown stream-ordered.
@@ -533,9 +555,45 @@ int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream)
         int rc = get_stream_ws(ctx, st, total, &ws);
         if (rc != BM_OK) return rc;
     }
+    // direct jobs now; tensor-core jobs: preparation kernels, then the cross
+    // term + top-K of every job in persistent launches (jobs of one class
+    // share a launch), then the float32 re-ranks
+    std::vector<int> tc_ids;
+    std::vector<TcArgs> args(n);
     for (int i = 0; i < n; ++i) {
-        int rc = enqueue_job(ctx, gs[i], reqs[i], static_cast<char*>(ws) + offs[i], st);
+        int rc;
+        if (!use_tc(ctx, gs[i])) {
+            rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, st);
+        } else {
+            rc = prep_job(ctx, gs[i], reqs[i], static_cast<char*>(ws) + offs[i], st, args[i]);
+            tc_ids.push_back(i);
+        }
         if (rc != BM_OK) return rc;
+    }
+    if (!tc_ids.empty()) {
+        auto key = [&](int i) {
+            const Geom& g = gs[i];
+            return std::make_tuple(g.dtype, g.Cp, g.p, g.h, g.s, g.K, g.L);
+        };
+        std::stable_sort(tc_ids.begin(), tc_ids.end(), [&](int a, int b) { return key(a) < key(b); });
+        std::vector<Geom> tg;
+        std::vector<TcArgs> ta;
+        for (int i : tc_ids) {
+            tg.push_back(gs[i]);
+            ta.push_back(args[i]);
+        }
+        int nl = 0;
+        cudaError_t e = timed(ctx, BM_STAGE_TC, st, [&] {
+            return launch_tc_batch(tg.data(), ta.data(), (int)tg.size(), st, &nl);
+        }, &nl);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
+        ctx->tc_jobs += tc_ids.size();
+        for (int i : tc_ids) {
+            int rc = finish_job(ctx, gs[i], reqs[i], args[i], st);
+            if (rc != BM_OK) return rc;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
         ctx->matches += 1;
         ctx->refs += (unsigned long long)gs[i].nR;
     }
@@ -603,7 +661,7 @@ int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset) {
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.a, ev.b);
         if (e != cudaSuccess && rc == BM_OK) rc = cuda_fail(e, "timing event");
-        ctx->tm_total.launches[ev.stage] += 1;
+        ctx->tm_total.launches[ev.stage] += ev.n;
         ctx->tm_total.ms[ev.stage] += ms;
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);

@@ -40,6 +40,7 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
 size_t plane_bytes(const Geom& g);       // one bf16 plane
 size_t nrm_bytes(const Geom& g);         // candidate norms
 size_t pool_bytes(const Geom& g);        // float32 candidate pool
+size_t nsp_bytes(const Geom& g);         // split candidate norms (16 bytes each)
 
 // ---- kernels (each launcher returns cudaGetLastError()) ----
 
@@ -51,8 +52,11 @@ cudaError_t launch_center(const Geom& g, const void* img, float* center, cudaStr
 // (a1) box filter of the squared centred image:
 //      nrm[y][x] = sum_{u,v<p, c<C} (X[y+u][x+v][c] - c0)^2
 //      int32 (uint8, exact) or float32 (float32, compensated summation).
+// nsp (nullable): the same values split into bf16 pieces for the tensor-core
+// norm K-step, column-major nsp[x][y][8]: uint8 (hi, mid, lo, 0...) exact,
+// float32 (hi, mid, lo, hi, mid, lo, 0, 0).
 cudaError_t launch_boxfilter(const Geom& g, const void* img, const float* center, void* nrm,
-                             cudaStream_t st);
+                             uint16_t* nsp, cudaStream_t st);
 
 // bf16 operand planes of the centred image: uint8 -> one exact plane;
 // float32 -> hi and lo planes with x - c0 ~= hi + lo (hi = RN_bf16, lo = RN_bf16(rest)).
@@ -70,6 +74,7 @@ struct TcArgs {
     const uint16_t* plane0;   // bf16 hi (or exact uint8) plane
     const uint16_t* plane1;   // bf16 lo plane (float32 only)
     const void* nrm;          // int32 or float32 norms [Hc][Wc]
+    const uint16_t* nsp;      // split norms [Wc][Hc][8] bf16 (launch_boxfilter)
     int32_t* out_idx;         // uint8: final indices
     int32_t* out_dist;        // uint8: final distances
     int32_t* pool_idx;        // float32: candidate pool offsets [nR][L]
@@ -77,9 +82,14 @@ struct TcArgs {
     int* status;              // device error word (0 = ok)
 };
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
-// Several jobs in persistent launches (consecutive jobs of one class share a launch).
-cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st);
+// Several jobs in persistent launches (consecutive jobs of one class share a
+// launch, up to 64 jobs each); *nlaunch (nullable) = kernel launches made.
+cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st,
+                            int* nlaunch = nullptr);
 bool tc_supported(const Geom& g);
+// float32 pool scores of the tensor-core pass are rounded up by less than
+// 2^bits ulp (0: exact float32 scores).
+int tc_score_bits(const Geom& g);
 bool tc_same_class(const Geom& a, const Geom& b);
 
 // (a6) float32 boundary re-rank: direct recomputation of the pool's band,

@@ -36,7 +36,7 @@ size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 // offset 16) and the re-rank counters (4 x u64, offset 32); the header is the
 // only part that must start at zero, and each call clears it.
 struct Layout {
-    size_t plane0, plane1, nrm, pool_idx, pool_score, total;
+    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, total;
 };
 constexpr size_t kHeader = 256;
 constexpr size_t kCenterOff = 16;
@@ -49,6 +49,7 @@ Layout layout(const Geom& g) {
         l.plane0 = off; off += round256(plane_bytes(g));
         l.plane1 = off; off += g.dtype == kF32 ? round256(plane_bytes(g)) : 0;
         l.nrm = off; off += round256(nrm_bytes(g));
+        l.nsp = off; off += round256(nsp_bytes(g));
         l.pool_idx = off; off += g.dtype == kF32 ? round256((size_t)g.nR * g.L * 4) : 0;
         l.pool_score = off; off += g.dtype == kF32 ? round256((size_t)g.nR * g.L * 4) : 0;
     }
@@ -140,17 +141,19 @@ extern "C" int bm_match_static(const void* img, int H, int W, int C, bm_dtype dt
     uint16_t* p0 = reinterpret_cast<uint16_t*>(b + l.plane0);
     uint16_t* p1 = g.dtype == kF32 ? reinterpret_cast<uint16_t*>(b + l.plane1) : nullptr;
     void* nrm = b + l.nrm;
+    uint16_t* nsp = reinterpret_cast<uint16_t*>(b + l.nsp);
     float* center = reinterpret_cast<float*>(b + kCenterOff);
     auto* counters = reinterpret_cast<unsigned long long*>(b + kCountersOff);
     if ((e = launch_center(g, img, center, st)) != cudaSuccess) return launch_fail(e, "centre kernel launch");
     if ((e = launch_planes(g, img, center, p0, p1, st)) != cudaSuccess)
         return launch_fail(e, "plane kernel launch");
-    if ((e = launch_boxfilter(g, img, center, nrm, st)) != cudaSuccess)
+    if ((e = launch_boxfilter(g, img, center, nrm, nsp, st)) != cudaSuccess)
         return launch_fail(e, "box filter launch");
     TcArgs a{};
     a.plane0 = p0;
     a.plane1 = p1;
     a.nrm = nrm;
+    a.nsp = nsp;
     a.status = reinterpret_cast<int*>(b);
     if (g.dtype == kU8) {
         a.out_idx = out_idx;

@@ -26,6 +26,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+// x = hi + mid + lo exactly for any float with <= 24 significant bits (the
+// norm pieces of the tensor-core norm K-step).
+__device__ __forceinline__ uint4 split_norm(float x, bool two_copies) {
+    const uint16_t hi = bf16_bits(x);
+    const float r1 = x - __bfloat162float(__ushort_as_bfloat16(hi));
+    const uint16_t mid = bf16_bits(r1);
+    const float r2 = r1 - __bfloat162float(__ushort_as_bfloat16(mid));
+    const uint16_t lo = bf16_bits(r2);
+    if (two_copies)
+        return make_uint4(hi | (uint32_t(mid) << 16), lo | (uint32_t(hi) << 16),
+                          mid | (uint32_t(lo) << 16), 0u);
+    return make_uint4(hi | (uint32_t(mid) << 16), lo, 0u, 0u);
+}
+
 // Compensated accumulator: value = hi + lo to about one float ulp.
 struct Acc2 {
     float hi, lo;
@@ -40,11 +57,13 @@ struct Acc2 {
 // One thread per output column; each block walks a strip of kBoxRows output
 // rows.  The last p row sums live in a per-thread shared-memory ring so every
 // image row is read once per column; output = sum of the p ring entries in
-// fixed order (deterministic).
+// fixed order (deterministic).  With nsp, each value is also written as its
+// bf16 pieces, column-major (a column of a chunk is one contiguous copy).
 template <bool kU8>
 __global__ void __launch_bounds__(kBoxThreads)
 boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int Wc,
-                 const float* __restrict__ center, void* __restrict__ nrm) {
+                 const float* __restrict__ center, void* __restrict__ nrm,
+                 uint4* __restrict__ nsp) {
     extern __shared__ unsigned char smem_raw[];
     const int x = blockIdx.x * kBoxThreads + threadIdx.x;
     if (x >= Wc) return;
@@ -67,6 +86,7 @@ boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int 
                 int sum = 0;
                 for (int u = 0; u < p; ++u) sum += ring[((yo + u) % p) * kBoxThreads + threadIdx.x];
                 static_cast<int*>(nrm)[(size_t)yo * Wc + x] = sum;
+                if (nsp) nsp[(size_t)x * Hc + yo] = split_norm((float)sum, false);
             }
         }
     } else {
@@ -92,7 +112,9 @@ boxfilter_kernel(const void* __restrict__ img, int W, int C, int p, int Hc, int 
                     s.add(r.x);
                     s.lo += r.y;
                 }
-                static_cast<float*>(nrm)[(size_t)yo * Wc + x] = s.hi + s.lo;
+                const float v = s.hi + s.lo;
+                static_cast<float*>(nrm)[(size_t)yo * Wc + x] = v;
+                if (nsp) nsp[(size_t)x * Hc + yo] = split_norm(v, true);
             }
         }
     }
@@ -184,14 +206,16 @@ cudaError_t launch_center(const Geom& g, const void* img, float* center, cudaStr
 }
 
 cudaError_t launch_boxfilter(const Geom& g, const void* img, const float* center, void* nrm,
-                             cudaStream_t st) {
+                             uint16_t* nsp, cudaStream_t st) {
     dim3 grid((g.Wc + kBoxThreads - 1) / kBoxThreads, (g.Hc + kBoxRows - 1) / kBoxRows);
     if (g.dtype == kU8) {
         size_t sm = (size_t)g.p * kBoxThreads * sizeof(int);
-        boxfilter_kernel<true><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm);
+        boxfilter_kernel<true><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm,
+                                                              reinterpret_cast<uint4*>(nsp));
     } else {
         size_t sm = (size_t)g.p * kBoxThreads * sizeof(float2);
-        boxfilter_kernel<false><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm);
+        boxfilter_kernel<false><<<grid, kBoxThreads, sm, st>>>(img, g.W, g.C, g.p, g.Hc, g.Wc, center, nrm,
+                                                              reinterpret_cast<uint4*>(nsp));
     }
     return cudaGetLastError();
 }

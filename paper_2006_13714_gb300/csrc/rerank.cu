@@ -12,7 +12,10 @@
 //      entries with u_j = v_j + eps n_r >= T' can be among the K nearest (the
 //      band).  If the pool is full and every entry is in the band,
 //      candidates outside the pool might qualify too ("overflow"): that
-//      reference is recomputed over its whole window.
+//      reference is recomputed over its whole window.  When the pool scores
+//      arrive rounded up (v'_j >= v_j, by less than 2^tbits ulp: the 32-bit
+//      keys of the tensor-core pass), T' also subtracts that rounding of the
+//      top-K entries.
 //   2. Band members get the explicit FP32 distance sum (X_r - X_j)^2
 //      (Eq. equ:bmMetric_app), relative error <= gamma = (n + 3) 2^-24 with
 //      n = p*p*C terms, and are ranked by (distance, row-major offset).
@@ -44,6 +47,7 @@ struct RerankParams {
     float* out_dist;
     unsigned long long* counters;  // [0] overflow, [1] fp64 rechecks, [2] bound violations
     int H, W, C, p, h, s, K, L, n_ry, n_rx, Wc, nR;
+    float round_rel;  // pool-score rounding, relative: 2^(tbits - 23) (0: exact scores)
 };
 
 __device__ __forceinline__ float direct_f32(const RerankParams& P, const float* ref, int yc, int xc) {
@@ -239,17 +243,21 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
             vk[i] = ((unsigned long long)(~orderable(v[i])) << 32) | (unsigned)(lane + 32 * i);
         int rk[S];
         warp_rank(vk, rk);
-        float vK = -__int_as_float(0x7f800000), ncmax = 0.f;
+        float vK = -__int_as_float(0x7f800000), ncmax = 0.f, vabs = 0.f;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             if (off[i] >= 0 && rk[i] == P.K - 1) vK = v[i];
-            if (off[i] >= 0 && rk[i] < P.K) ncmax = fmaxf(ncmax, nc[i]);
+            if (off[i] >= 0 && rk[i] < P.K) {
+                ncmax = fmaxf(ncmax, nc[i]);
+                vabs = fmaxf(vabs, fabsf(v[i]));
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             vK = fmaxf(vK, __shfl_xor_sync(0xffffffffu, vK, o));
             ncmax = fmaxf(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
+            vabs = fmaxf(vabs, __shfl_xor_sync(0xffffffffu, vabs, o));
         }
-        const float tb = vK - 2.0f * kEps * (nr + ncmax) * 1.0001f;
+        const float tb = vK - P.round_rel * vabs * 1.001f - 2.0f * kEps * (nr + ncmax) * 1.0001f;
         int cnt = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
@@ -272,8 +280,8 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
                 key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)off[i];
                 // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
                 const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
-                if (fabsf(dt - d32) >
-                    2.0f * kEps * (nr + nc[i]) + gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
+                if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + 2.0f * P.round_rel * fabsf(v[i]) +
+                                          gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
                     ++viol;
             }
         }
@@ -346,6 +354,8 @@ cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
     P.out_idx = out_idx; P.out_dist = out_dist; P.counters = counters;
     P.H = g.H; P.W = g.W; P.C = g.C; P.p = g.p; P.h = g.h; P.s = g.s; P.K = g.K; P.L = g.L;
     P.n_ry = g.n_ry; P.n_rx = g.n_rx; P.Wc = g.Wc; P.nR = g.nR;
+    const int tb = tc_score_bits(g);
+    P.round_rel = tb ? ldexpf(1.0f, tb - 23) : 0.0f;
     const int blocks = (g.nR + kWarps - 1) / kWarps;
     switch ((g.L + 31) / 32) {
         case 1: rerank_kernel<1><<<blocks, kWarps * 32, 0, st>>>(P); break;

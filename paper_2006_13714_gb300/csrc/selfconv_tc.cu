@@ -1,9 +1,9 @@
 // selfconv_tc.cu -- (a3)-(a5): tcgen05 Self-Convolution cross term with the
 // distance assembly and the per-reference top-K fused into the epilogue.
 //
-// What one CTA computes.  A tile of 128 reference patches (4 reference rows x
-// 32 reference columns of the stride-s grid).  For every candidate j in the
-// union of their search windows the tensor cores produce, per reference r,
+// What one tile computes.  128 reference patches (a ty x tx block of the
+// stride-s reference grid).  For every candidate j in the union of their
+// search windows the tensor cores produce, per reference r,
 //
 //   v(r, j) = <X_r, X_j> - c * n_j          (n_j = ||X_j||^2, the box filter)
 //
@@ -13,7 +13,8 @@
 // b = vec(C_r) - 0.5 h_X (.) h_X: the K largest entries of b are the K
 // nearest candidates, and d = ||X_r||^2 - 2 b (Lemma 2).  The norm term is an
 // extra K-step of the same MMA (A = constant coefficients, B = n_j split into
-// three bf16 pieces), so TMEM already holds the score.
+// three bf16 pieces, precomputed by the box filter), so TMEM already holds
+// the score.
 //
 //   uint8 : operands are centred (x - 128) and A is doubled, all exact in
 //           bf16; products and every partial sum are integers below 2^24
@@ -27,45 +28,46 @@
 //           (|b~ - b| <= eps (n_r + n_j), eps = 2^-14).  Output: a pool of the
 //           L largest v per reference for the boundary re-rank kernel.
 //
-// Operand layout (no im2col in HBM).  A (references) is K-major in the
-// canonical no-swizzle core-matrix layout, staged once per CTA.  B
-// (candidates) is formed in shared memory per chunk of candidate columns as
-// "column strips": for candidate column j and 16-byte chunk q of a patch row,
-// strip[q][j][row] holds the 8 elements starting at pixel (X0 + j) of image
-// row (Y0 + row).  Candidate n = j * Rb + row (column-major) then reads patch
-// row u at strip[q][j][row + u]: eight consecutive candidates are eight
-// consecutive 16-byte rows -- exactly a no-swizzle K-major core matrix -- so
-// every K-step is a plain descriptor with SBO = 128 B and LBO = 16 B (next
-// patch row) or the q-strip pitch (next chunk of the same row).
+// Data movement (no im2col in HBM).  Per tile, TMA (cp.async.bulk.tensor)
+// stages the image tile plus its window halo -- the union of the tile's
+// candidate patches -- from each bf16 plane into shared memory.  The
+// references' A operand (K-major, canonical no-swizzle core-matrix layout)
+// is cut from that staged tile.  Candidates are formed in place, per chunk
+// of candidate columns, as "column strips": for candidate column j and
+// 16-byte chunk q of a patch row, strip[q][j][row] holds the 8 elements
+// starting at pixel (X0 + j) of image row (Y0 + row).  Candidate
+// n = j * Rb + row (column-major) then reads patch row u at
+// strip[q][j][row + u]: eight consecutive candidates are eight consecutive
+// 16-byte rows -- a no-swizzle K-major core matrix -- so every K-step is a
+// plain descriptor with SBO = 128 B and LBO = 16 B (next patch row) or the
+// q-strip pitch (next chunk of the same row).  The split norms of a chunk's
+// columns arrive by bulk copy (cp.async.bulk), one contiguous column each.
 //
-// Warp roles: warps 0..EW-1 epilogue (warp w reads TMEM lanes 32(w%4)..+31;
-// with EW = 8 two warps share each lane quarter and take alternate candidate
-// columns, each keeping its own list, merged at the end of the tile), the
-// next three warps producers (strip formation from the bf16 planes), the last
-// warp TMEM allocation + single-thread MMA issue.
-// Pipelines: kStages shared-memory stages (mbarriers full/empty) and two
-// 256-column TMEM accumulators (tfull/tempty).  Every wait is bounded; on
-// timeout the CTA sets *status, drains and frees its TMEM.
+// Slots.  A CTA keeps NS tiles in flight.  Slot k owns epilogue warps
+// 4k..4k+3 (warp 4k+i reads TMEM lanes 32i..32i+31), one control warp
+// (TMA issue, operand formation, single-thread MMA issue), its own shared-
+// memory regions and two TMEM accumulators, so the slots never wait on each
+// other; they share only the tensor core.  Every wait is bounded; on timeout
+// the CTA sets *status, waits for its copies and MMAs in flight, frees its
+// TMEM and returns.
 #include "bm_internal.h"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 namespace bm {
 namespace {
 
-constexpr int kProducers = 96;  // three producer warps
-// Threads of a CTA with EW epilogue warps: EW + 3 producer warps + 1 MMA warp.
-template <int EW>
-__host__ __device__ constexpr int cta_threads() { return EW * 32 + kProducers + 32; }
-constexpr int kStages = 3;
 constexpr int kTmemCols = 512;
-constexpr int kBufCols = 256;
 constexpr float kEps = 6.103515625e-05f;  // 2^-14
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kBuf = 32;   // per-lane append buffer (entries) between merges
 constexpr int kBatch = 8;  // keys merged into the register list at a time
+constexpr int kMaxSt = 3;  // stages per slot (upper bound)
+
+// Threads of a CTA with NS slots: 4 epilogue warps + 1 control warp per slot.
+__host__ __device__ constexpr int cta_threads(int ns) { return ns * 160; }
 
 // Class-wide geometry of one launch (every job shares patch, window, stride,
 // K, channel padding and dtype; image sizes are per job).
@@ -73,26 +75,31 @@ struct TcGeom {
     int Cp, p, h, s, K, HL;
     int rr, rc, wgx, ty, tx;  // lane -> reference mapping and tile shape (references)
     int pw, p_eff, nkc, Rb, kcols;
-    int nslots, bufcols;      // tiles in flight per CTA, TMEM columns per accumulator
-    int qpitch, plane_stage, ns_bytes, stage_bytes;
+    int nslots, bufcols, nst; // tiles in flight, TMEM columns per accumulator, stages per slot
+    int kbuf;                 // append-buffer entries per lane
+    int tbits;                // float32 32-bit keys: window-index bits (0: 64-bit keys)
+    int nc_box, base_pitch, base_bytes;  // staged tile: 16-byte chunks per row, row pitch, bytes per plane
+    int qpitch, plane_stage, stage_bytes;
     int f32;
-    int off_a, a_bytes, off_an, off_stage, off_heap, off_buf, off_bar, smem_total;
+    int a_bytes;
+    int off_base, off_a, off_stage, off_buf, slot_bytes;  // inside a slot's region
+    int off_slots, off_an, off_heap, off_bar, smem_total;
 };
 
 // One image of a launch.
 struct TcJob {
-    const uint16_t* plane0;
-    const uint16_t* plane1;
-    const void* nrm;
-    int32_t* out_idx;     // uint8: final indices
-    int32_t* out_dist;    // uint8: final distances
-    int32_t* pool_idx;    // float32: pool
+    CUtensorMap map[2];       // bf16 planes (hi / exact, lo) as {8 elements, row chunks, rows}
+    const uint16_t* nsp;      // split norms [Wc][Hc][8] bf16
+    const void* nrm;          // int32 / float32 norms [Hc][Wc]
+    int32_t* out_idx;         // uint8: final indices
+    int32_t* out_dist;        // uint8: final distances
+    int32_t* pool_idx;        // float32: pool
     float* pool_score;
-    int H, W, n_ry, n_rx, Hc, Wc, plane_pitch;
+    int H, W, n_ry, n_rx, Hc, Wc;
     int tiles_x, tile_begin;  // tiles along x; index of the job's first tile
 };
 
-constexpr int kMaxJobs = 160;  // jobs per launch (kept inline in the kernel parameters)
+constexpr int kMaxJobs = 64;  // jobs per launch (kept inline in the kernel parameters)
 
 struct TcParams {
     TcGeom g;
@@ -201,39 +208,6 @@ __device__ __forceinline__ void tmem_ld_blocks<1>(uint32_t taddr, float* v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-template <>
-__device__ __forceinline__ void tmem_ld_blocks<2>(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr + 0u), "r"(taddr + 16u)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-template <>
-__device__ __forceinline__ void tmem_ld_blocks<4>(uint32_t taddr, float* v) {
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%65];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%66];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%67];\n\t"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ float max3(float a, float b, float c) {
-    float m;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
-    return m;
-}
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
 // LBO = byte step between K-adjacent core matrices, SBO = between M/N-adjacent.
@@ -253,15 +227,6 @@ __device__ __forceinline__ uint16_t bf16_bits(float x) {
 __device__ __forceinline__ float bf16_val(uint16_t b) {
     return __bfloat162float(__ushort_as_bfloat16(b));
 }
-// x = hi + mid + lo exactly for any float with <= 24 significant bits.
-__device__ __forceinline__ void split3(float x, uint16_t& hi, uint16_t& mid, uint16_t& lo) {
-    hi = bf16_bits(x);
-    float r1 = x - bf16_val(hi);
-    mid = bf16_bits(r1);
-    float r2 = r1 - bf16_val(mid);
-    lo = bf16_bits(r2);
-}
-
 __device__ __forceinline__ unsigned orderable(float f) {
     unsigned b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -270,25 +235,94 @@ __device__ __forceinline__ float from_orderable(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-// 16 bytes of a bf16 plane row starting at element e0 (any alignment).
-__device__ __forceinline__ uint4 load_shifted16(const uint16_t* row, int e0) {
-    const int a0 = e0 & ~7, sh = e0 & 7;
-    const uint4 A = __ldg(reinterpret_cast<const uint4*>(row + a0));
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+// TMA: 3-D tiled tensor load global -> shared, completion on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+// Bulk (non-tensor) copy global -> shared; 16-byte aligned, size % 16 == 0.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// 16 bytes starting SH bf16 elements into the 32 bytes {a, b}.
+template <int SH>
+__device__ __forceinline__ uint4 shift_words(const uint4& a, const uint4& b) {
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    constexpr int j = SH >> 1;
+    if constexpr ((SH & 1) != 0)
+        return make_uint4(__funnelshift_r(w[j], w[j + 1], 16), __funnelshift_r(w[j + 1], w[j + 2], 16),
+                          __funnelshift_r(w[j + 2], w[j + 3], 16), __funnelshift_r(w[j + 3], w[j + 4], 16));
+    else
+        return make_uint4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+}
+
+// 16 bytes of a staged row starting at element e (any alignment; per-lane e).
+__device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
+    const uint4* s = reinterpret_cast<const uint4*>(row + (e >> 3) * 16);
+    const uint4 A = s[0];
+    const int sh = e & 7;
     if (sh == 0) return A;
-    const uint4 B = __ldg(reinterpret_cast<const uint4*>(row + a0 + 8));
+    const uint4 B = s[1];
     const uint32_t w[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
     const int j = sh >> 1;
-    uint32_t s[5];
+    uint32_t v[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
-        s[i] = j == 0 ? w[i] : j == 1 ? w[i + 1] : j == 2 ? w[i + 2] : w[i + 3];
+        v[i] = j == 0 ? w[i] : j == 1 ? w[i + 1] : j == 2 ? w[i + 2] : w[i + 3];
     const uint32_t f = (sh & 1) * 16;
-    uint4 o;
-    o.x = __funnelshift_r(s[0], s[1], f);
-    o.y = __funnelshift_r(s[1], s[2], f);
-    o.z = __funnelshift_r(s[2], s[3], f);
-    o.w = __funnelshift_r(s[3], s[4], f);
-    return o;
+    return make_uint4(__funnelshift_r(v[0], v[1], f), __funnelshift_r(v[1], v[2], f),
+                      __funnelshift_r(v[2], v[3], f), __funnelshift_r(v[3], v[4], f));
+}
+
+// Strip rows [lane, Rb) step 32: dst row = 16 bytes of staged row `row`
+// starting SH elements past src (the shift is the same for the whole strip).
+template <int SH>
+__device__ __forceinline__ void copy_strip(const uint8_t* src, int pitch, uint8_t* dst, int Rb,
+                                           int lane) {
+    // Rb is a multiple of 16: rows lane, lane + 32, ... two loads in flight
+    for (int r0 = 0; r0 < Rb; r0 += 64) {
+        const int row0 = r0 + lane, row1 = row0 + 32;
+        uint4 a0 = make_uint4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
+        if (row0 < Rb) {
+            const uint4* s = reinterpret_cast<const uint4*>(src + row0 * pitch);
+            a0 = s[0];
+            b0 = SH ? s[1] : a0;
+        }
+        if (row1 < Rb) {
+            const uint4* s = reinterpret_cast<const uint4*>(src + row1 * pitch);
+            a1 = s[0];
+            b1 = SH ? s[1] : a1;
+        }
+        if (row0 < Rb) *reinterpret_cast<uint4*>(dst + row0 * 16) = shift_words<SH>(a0, b0);
+        if (row1 < Rb) *reinterpret_cast<uint4*>(dst + row1 * 16) = shift_words<SH>(a1, b1);
+    }
+}
+
+__device__ __forceinline__ void copy_strip_any(int sh, const uint8_t* src, int pitch, uint8_t* dst,
+                                               int Rb, int lane) {
+    switch (sh) {
+        case 0: copy_strip<0>(src, pitch, dst, Rb, lane); break;
+        case 1: copy_strip<1>(src, pitch, dst, Rb, lane); break;
+        case 2: copy_strip<2>(src, pitch, dst, Rb, lane); break;
+        case 3: copy_strip<3>(src, pitch, dst, Rb, lane); break;
+        case 4: copy_strip<4>(src, pitch, dst, Rb, lane); break;
+        case 5: copy_strip<5>(src, pitch, dst, Rb, lane); break;
+        case 6: copy_strip<6>(src, pitch, dst, Rb, lane); break;
+        default: copy_strip<7>(src, pitch, dst, Rb, lane); break;
+    }
 }
 
 // 4-ary max-heap of u64 keys per epilogue thread, element i at h[i * 128]
@@ -338,9 +372,14 @@ __device__ __forceinline__ void cmpx(unsigned long long& x, unsigned long long& 
     x = lo;
     y = hi;
 }
+__device__ __forceinline__ void cmpx(unsigned& x, unsigned& y) {
+    const unsigned lo = min(x, y), hi = max(x, y);
+    x = lo;
+    y = hi;
+}
 // Bitonic sort of N registers, ascending.
-template <int N>
-__device__ __forceinline__ void bitonic_sort(unsigned long long (&v)[N]) {
+template <int N, class T>
+__device__ __forceinline__ void bitonic_sort(T (&v)[N]) {
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1)
 #pragma unroll
@@ -355,8 +394,8 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long (&v)[N]) {
             }
 }
 // Sort a bitonic sequence of N registers, ascending.
-template <int N>
-__device__ __forceinline__ void bitonic_merge(unsigned long long (&v)[N]) {
+template <int N, class T>
+__device__ __forceinline__ void bitonic_merge(T (&v)[N]) {
 #pragma unroll
     for (int j = N >> 1; j > 0; j >>= 1)
 #pragma unroll
@@ -372,16 +411,16 @@ __device__ __forceinline__ void bitonic_merge(unsigned long long (&v)[N]) {
 // bitonic merge restores the order -- far fewer compare-exchanges per key
 // than a full insertion pass per key.  Entries 0..cap-1 are the
 // answer (cap <= LC); extra entries only make the list a superset.
-template <int LC>
+template <int LC, class T = unsigned long long>
 struct RegTopK {
-    unsigned long long a[LC];
+    T a[LC];
     int cap;
     __device__ __forceinline__ void init(int c) {
         cap = c;
 #pragma unroll
-        for (int i = 0; i < LC; ++i) a[i] = kEmpty;
+        for (int i = 0; i < LC; ++i) a[i] = ~T(0);
     }
-    __device__ __forceinline__ void merge_batch(unsigned long long (&b)[kBatch]) {
+    __device__ __forceinline__ void merge_batch(T (&b)[kBatch]) {
         bitonic_sort<kBatch>(b);
 #pragma unroll
         for (int i = 0; i < LC; ++i) {
@@ -390,16 +429,42 @@ struct RegTopK {
         }
         bitonic_merge<LC>(a);
     }
-    __device__ __forceinline__ unsigned long long kth() const {  // entry cap-1
-        unsigned long long r = 0;
+    __device__ __forceinline__ T kth() const {  // entry cap-1
+        T r = 0;
 #pragma unroll
         for (int i = 0; i < LC; ++i) {
-            const unsigned long long x = i < cap ? a[i] : 0ull;
+            const T x = i < cap ? a[i] : T(0);
             r = x > r ? x : r;
         }
         return r;
     }
 };
+
+// float32 pool with 32-bit keys: key = (~orderable(v) with its low tbits
+// bits cleared) | window index of the candidate, so one min/max pair is a
+// compare-exchange.  The cleared bits round v up by less than 2^tbits ulp
+// (v' = from_orderable(~(key & ~M)) >= v); the re-rank widens its band by
+// that amount.
+__device__ __forceinline__ void merge_pending32(unsigned* pend, int& cnt, float& thr,
+                                                RegTopK<32, unsigned>& reg, unsigned M) {
+    const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    for (int j0 = 0; j0 < m; j0 += kBatch) {
+        unsigned b[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) b[t] = j0 + t < cnt ? pend[(j0 + t) * 128] : ~0u;
+        reg.merge_batch(b);
+    }
+    cnt = 0;
+    const unsigned t = reg.kth();
+    // lowest value whose key can still beat the list's last entry
+    if (t != ~0u) thr = from_orderable(~(t | M));
+}
+__device__ __noinline__ RegTopK<32, unsigned> final_merge32(unsigned* pend, int cnt,
+                                                            RegTopK<32, unsigned> reg, unsigned M) {
+    float thr = 0.f;
+    merge_pending32(pend, cnt, thr, reg, M);
+    return reg;
+}
 
 // Warp-synchronous merge of every lane's pending entries (call from all 32
 // lanes): one pending entry per lane per step goes through the selection.
@@ -515,57 +580,65 @@ __device__ __forceinline__ int slot_tile(int b, int g, int k, int nslots, int gr
     return b + (g * nslots + k) * grid;
 }
 
+// Barriers of one slot (index into the slot's block of kBarsPerSlot).
+enum : int {
+    kBarBase = 0,                 // staged tile landed (TMA, tx count)
+    kBarAEmpty = 1,               // MMAs of the previous tile done with A
+    kBarDone = 2,                 // drain: every MMA of the slot finished
+    kBarTFull = 3,                // [2] accumulator ready for the epilogue
+    kBarTEmpty = 5,               // [2] accumulator drained by the epilogue (128 arrivals)
+    kBarSEmpty = 7,               // [kMaxSt] stage free (MMAs done reading it)
+    kBarNFull = 7 + kMaxSt,       // [kMaxSt] stage's split norms landed (bulk copy, tx count)
+    kBarsPerSlot = 7 + 2 * kMaxSt
+};
+
+// Bounded wait that ignores the abort flag (draining copies in flight).
+__device__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity) && globaltimer() - t0 < kWaitNs) {
+    }
+}
+
 // ---------------------------------------------------------------- the kernel
 //
 // Persistent: CTA b walks the tiles b, b + G, b + 2G, ... of every job of
-// the launch, NS tiles in flight ("slots").  Slot k owns epilogue warps
-// 4k..4k+3, its own A operand region and two TMEM accumulators; the
-// producers and the MMA thread alternate between the slots' chunks, so the
-// epilogue of one tile overlaps the MMAs of the other.
-template <int LC, bool F32, int NS>
-__global__ void __launch_bounds__(cta_threads<4 * NS>(), 1)
+// the launch, NS tiles in flight (slot k takes turns k, k + NS, ...).
+template <int LC, bool F32, int NS, bool K32>
+__global__ void __launch_bounds__(cta_threads(NS), 1)
 tc_match_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const TcGeom& G = P.g;
     constexpr bool kF32 = F32;
-    constexpr int EW = 4 * NS;
-    constexpr int kThreads = cta_threads<EW>();
-    constexpr int kMmaWarp = EW + 3;
-    constexpr int kEpi = EW * 32;  // epilogue threads (pending-buffer stride)
+    constexpr int kEpiWarps = 4 * NS;
+    constexpr int kThreads = cta_threads(NS);
     constexpr int nplanes = kF32 ? 2 : 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grid = gridDim.x, cta = blockIdx.x;
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G.off_bar);
-    // barrier slots: full[kStages], empty[kStages], tfull[NS][2], tempty[NS][2],
-    // afull[NS], aempty[NS], done
-    const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kStages);
-    const uint32_t bar_tfull = smem_u32(bars + 2 * kStages);
-    const uint32_t bar_tempty = smem_u32(bars + 2 * kStages + 2 * NS);
-    const uint32_t bar_afull = smem_u32(bars + 2 * kStages + 4 * NS);
-    const uint32_t bar_aempty = smem_u32(bars + 2 * kStages + 5 * NS);
-    const uint32_t bar_done = smem_u32(bars + 2 * kStages + 6 * NS);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6 * NS + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NS * kBarsPerSlot);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t bar0 = smem_u32(bars);
+    auto BAR = [bar0](int k, int i) -> uint32_t { return bar0 + 8u * (uint32_t)(k * kBarsPerSlot + i); };
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
-            mbar_init(bar_full + 8 * i, kProducers);
-            mbar_init(bar_empty + 8 * i, 1);
-        }
-        for (int i = 0; i < 2 * NS; ++i) {
-            mbar_init(bar_tfull + 8 * i, 1);
-            mbar_init(bar_tempty + 8 * i, 128);
-        }
         for (int k = 0; k < NS; ++k) {
-            mbar_init(bar_afull + 8 * k, kProducers);
-            mbar_init(bar_aempty + 8 * k, 1);
+            mbar_init(BAR(k, kBarBase), 1);
+            mbar_init(BAR(k, kBarAEmpty), 1);
+            mbar_init(BAR(k, kBarDone), 1);
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(BAR(k, kBarTFull + b), 1);
+                mbar_init(BAR(k, kBarTEmpty + b), 128);
+            }
+            for (int i = 0; i < kMaxSt; ++i) {
+                mbar_init(BAR(k, kBarSEmpty + i), 1);
+                mbar_init(BAR(k, kBarNFull + i), 1);
+            }
         }
-        mbar_init(bar_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    if (warp == kEpiWarps) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
     // A_norm (shared by all tiles): [group][2 kchunks][8 x 16 B], the
     // coefficients of the norm pieces
     for (int t = threadIdx.x; t < 128 * 2; t += kThreads) {
@@ -580,68 +653,94 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                                      c[4] | (uint32_t(c[5]) << 16), c[6] | (uint32_t(c[7]) << 16));
         *reinterpret_cast<uint4*>(smem + G.off_an + (m >> 3) * 256 + kc * 128 + (m & 7) * 16) = val;
     }
-    // stage buffers start zeroed so padding rows are finite
-    for (int t = threadIdx.x; t < kStages * G.stage_bytes / 16; t += kThreads)
-        reinterpret_cast<uint4*>(smem + G.off_stage)[t] = make_uint4(0, 0, 0, 0);
+    // stages start zeroed: rows no copy writes stay finite
+    for (int k = 0; k < NS; ++k)
+        for (int t = threadIdx.x; t < G.nst * G.stage_bytes / 16; t += kThreads)
+            reinterpret_cast<uint4*>(smem + G.off_slots + k * G.slot_bytes + G.off_stage)[t] =
+                make_uint4(0, 0, 0, 0);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp >= EW && warp < kMmaWarp) {
-        // ------------------------------------------------------------ producers
-        const int pt = threadIdx.x - kEpi;
-        const int strip_items = nplanes * G.pw * G.kcols * G.Rb;
-        const int norm_items = G.kcols * G.Rb;
-        TileInfo ti[NS];
-        int chunk[NS], turn[NS];
-        bool active[NS];
-        for (int k = 0; k < NS; ++k) {
-            turn[k] = 0;
-            chunk[k] = 0;
-            const int t = slot_tile(cta, 0, k, NS, grid);
-            active[k] = t < P.total_tiles;
-            if (active[k]) ti[k] = tile_info(P, t);
-        }
-        int step = 0, next = 0;
+    if (warp >= kEpiWarps) {
+        // ------------------------------------------------------------ control warp of slot k
+        const int k = warp - kEpiWarps;
+        uint8_t* slot = smem + G.off_slots + k * G.slot_bytes;
+        uint8_t* sbase = slot + G.off_base;
+        uint8_t* sa = slot + G.off_a;
+        const uint32_t an = smem_u32(smem + G.off_an);
+        const uint32_t sbo_a = G.nkc * 128;
+        const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
+        const uint32_t box_bytes = (uint32_t)G.nc_box * 16u * (uint32_t)G.Rb;
+        // copies in flight (for the drain on abort): base phase, norm phase per stage
+        int base_pending = -1;
+        int norm_pending[kMaxSt];
+        for (int i = 0; i < kMaxSt; ++i) norm_pending[i] = -1;
+        int cs = 0;  // slot-local chunk counter: stage ring and accumulator phases
         bool ok = true;
-        while (ok) {
-            int k = next;
-            if (!active[k]) k = NS - 1 - k;
-            if (!active[k]) break;
-            next = NS - 1 - k;
-            const TileInfo& T = ti[k];
+        // Split norms of chunk c of tile T into stage (cs' % nst): one bulk
+        // copy per candidate column (rows Y0 .. min(Y0 + Rb, Hc) - 1).
+        auto issue_norm = [&](const TileInfo& T, int c, int csn) -> bool {
+            const int st = csn % G.nst, use = csn / G.nst;
+            if (use > 0 && !mbar_wait(BAR(k, kBarSEmpty + st), (use - 1) & 1, abort_flag, 1)) return false;
             const TcJob& J = *T.job;
-            if (chunk[k] == 0) {
-                // new tile for slot k: stage its A operand once the previous
-                // tile's MMAs are done with the region
-                if (turn[k] > 0 && !mbar_wait(bar_aempty + 8 * k, (turn[k] - 1) & 1, abort_flag, 5)) {
-                    ok = false;
-                    break;
-                }
-                const int items = 128 * G.nkc * nplanes;
-                for (int t0 = pt; t0 < items; t0 += 4 * kProducers) {
-                    uint4 val[4];
-                    int dst[4];
-#pragma unroll
-                    for (int u4 = 0; u4 < 4; ++u4) {
-                        const int t = t0 + u4 * kProducers;
-                        dst[u4] = -1;
-                        val[u4] = make_uint4(0, 0, 0, 0);
-                        if (t >= items) continue;
-                        const int pl = t / (128 * G.nkc), it = t % (128 * G.nkc);
-                        const int m = it / G.nkc, kc = it % G.nkc;
-                        const int u = kc / G.pw, q = kc % G.pw;
-                        const int mw = m >> 5, ml = m & 31;
-                        const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
-                        const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
-                        dst[u4] = k * G.a_bytes * nplanes + pl * G.a_bytes +
-                                  (m >> 3) * G.nkc * 128 + kc * 128 + (m & 7) * 16;
-                        if (ry < J.n_ry && rx < J.n_rx && u < G.p) {
-                            const uint16_t* plane = pl ? J.plane1 : J.plane0;
-                            const uint16_t* row = plane + (size_t)(ry * G.s + u) * J.plane_pitch;
-                            uint4 v = load_shifted16(row, rx * G.s * G.Cp + 8 * q);
+            const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+            const int kc_here = min(G.kcols, T.NX - jc0);
+            const int rows = min(G.Rb, J.Hc - T.Y0);
+            if (lane == 0) {
+                uint8_t* nsb = slot + G.off_stage + st * G.stage_bytes + nplanes * G.plane_stage;
+                mbar_arrive_expect_tx(BAR(k, kBarNFull + st), (uint32_t)(kc_here * rows * 16));
+                for (int jl = 0; jl < kc_here; ++jl)
+                    bulk_load(smem_u32(nsb + jl * G.Rb * 16),
+                              J.nsp + ((size_t)(T.X0 + jc0 + jl) * J.Hc + T.Y0) * 8,
+                              (uint32_t)(rows * 16), BAR(k, kBarNFull + st));
+            }
+            norm_pending[st] = use & 1;
+            return true;
+        };
+        for (int turn = 0; ok && !*abort_flag; ++turn) {
+            const int tile = slot_tile(cta, turn, k, NS, grid);
+            if (tile >= P.total_tiles) break;
+            const TileInfo T = tile_info(P, tile);
+            const TcJob& J = *T.job;
+            const int e0 = (T.X0 * G.Cp) & ~7, delta = T.X0 * G.Cp - e0;
+            // (1) stage the tile plus halo (this warp is done reading the previous one)
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive_expect_tx(BAR(k, kBarBase), nplanes * box_bytes);
+                for (int pl = 0; pl < nplanes; ++pl)
+                    tma_load_3d(smem_u32(sbase + pl * G.base_bytes), &J.map[pl], 0, e0 >> 3, T.Y0,
+                                BAR(k, kBarBase));
+            }
+            base_pending = turn & 1;
+            // (2) norms of the first chunk
+            ok = __all_sync(0xffffffffu, issue_norm(T, 0, cs));
+            // (3) A region free (previous tile's MMAs done) and the tile landed
+            if (ok && turn > 0) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarAEmpty), (turn - 1) & 1, abort_flag, 5));
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6));
+            if (!ok) break;
+            base_pending = -1;
+            // (4) A: reference patch rows cut from the staged tile; lane m
+            // takes references m, m + 32, ... (lane -> reference mapping of
+            // the epilogue), kc = patch row u, 16-byte chunk q
+            for (int m = lane; m < 128; m += 32) {
+                const int mw = m >> 5, ml = m & 31;
+                const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
+                const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
+                const bool ref_ok = ry < J.n_ry && rx < J.n_rx;
+                const int row0 = ry * G.s - T.Y0;
+                const int ecol0 = delta + (rx * G.s - T.X0) * G.Cp;
+                for (int pl = 0; pl < nplanes; ++pl) {
+                    const uint8_t* bp = sbase + pl * G.base_bytes;
+                    uint8_t* ap = sa + pl * G.a_bytes + (m >> 3) * G.nkc * 128 + (m & 7) * 16;
+                    int u = 0, q = 0;
+                    for (int kc = 0; kc < G.nkc; ++kc) {
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (ref_ok && u < G.p) {
+                            v = lds_shifted16(bp + (row0 + u) * G.base_pitch, ecol0 + 8 * q);
                             // zero the elements beyond the patch row (p * Cp elements)
                             const int valid = G.p * G.Cp - 8 * q;
                             uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -656,162 +755,84 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                                     w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
                                 }
                             }
-                            val[u4] = make_uint4(w[0], w[1], w[2], w[3]);
+                            v = make_uint4(w[0], w[1], w[2], w[3]);
                         }
+                        *reinterpret_cast<uint4*>(ap + kc * 128) = v;
+                        if (++q == G.pw) { q = 0; ++u; }
                     }
-#pragma unroll
-                    for (int u4 = 0; u4 < 4; ++u4)
-                        if (dst[u4] >= 0)
-                            *reinterpret_cast<uint4*>(smem + G.off_a + dst[u4]) = val[u4];
+                }
+            }
+            // (5) chunks of candidate columns
+            for (int c = 0; c < T.nchunks; ++c, ++cs) {
+                const int stage = cs % G.nst, use = cs / G.nst;
+                uint8_t* sb = slot + G.off_stage + stage * G.stage_bytes;
+                const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                const int kc_here = min(G.kcols, T.NX - jc0);
+                // strips (the stage was freed before its norms were issued)
+                for (int pl = 0; pl < nplanes; ++pl)
+                    for (int q = 0; q < G.pw; ++q)
+                        for (int jl = 0; jl < kc_here; ++jl) {
+                            const int ecol = delta + (jc0 + jl) * G.Cp + 8 * q;
+                            copy_strip_any(ecol & 7, sbase + pl * G.base_bytes + (ecol >> 3) * 16,
+                                           G.base_pitch,
+                                           sb + pl * G.plane_stage + q * G.qpitch + jl * G.Rb * 16,
+                                           G.Rb, lane);
+                        }
+                // norms of the next chunk of this tile
+                if (c + 1 < T.nchunks && !__all_sync(0xffffffffu, issue_norm(T, c + 1, cs + 1))) {
+                    ok = false;
+                    break;
                 }
                 fence_proxy_async();
-                mbar_arrive(bar_afull + 8 * k);
-            }
-            // one chunk of candidate columns of slot k's tile
-            const int stage = step % kStages, use = step / kStages;
-            if (use > 0 && !mbar_wait(bar_empty + 8 * stage, (use - 1) & 1, abort_flag, 1)) break;
-            uint8_t* sb = smem + G.off_stage + stage * G.stage_bytes;
-            const int jc0 = chunk_order(chunk[k], T.nchunks, T.center_chunk) * G.kcols;
-            const int kc_here = min(G.kcols, T.NX - jc0);
-            for (int t0 = pt; t0 < strip_items; t0 += 4 * kProducers) {
-                uint4 val[4];
-                int dst[4];
-#pragma unroll
-                for (int u4 = 0; u4 < 4; ++u4) {
-                    const int t = t0 + u4 * kProducers;
-                    dst[u4] = -1;
-                    val[u4] = make_uint4(0, 0, 0, 0);
-                    if (t >= strip_items) continue;
-                    int r = t;
-                    const int row = r % G.Rb; r /= G.Rb;
-                    const int jl = r % G.kcols; r /= G.kcols;
-                    const int q = r % G.pw;
-                    const int pl = r / G.pw;
-                    if (jl >= kc_here) continue;
-                    dst[u4] = pl * G.plane_stage + q * G.qpitch + (jl * G.Rb + row) * 16;
-                    if (row < T.NR + G.p_eff - 1) {  // rows past that feed no real candidate
-                        const uint16_t* plane = pl ? J.plane1 : J.plane0;
-                        const uint16_t* prow = plane + (size_t)(T.Y0 + row) * J.plane_pitch;
-                        val[u4] = load_shifted16(prow, (T.X0 + jc0 + jl) * G.Cp + 8 * q);
+                __syncwarp();
+                int lok = 1;
+                if (lane == 0) {
+                    const int buf = cs & 1, ub = cs >> 1;
+                    if (ub > 0 && !mbar_wait(BAR(k, kBarTEmpty + buf), (ub - 1) & 1, abort_flag, 2)) lok = 0;
+                    if (lok && !mbar_wait(BAR(k, kBarNFull + stage), use & 1, abort_flag, 3)) lok = 0;
+                    if (lok) {
+                        tc_fence_after();
+                        const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
+                        const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
+                        const uint32_t sbu = smem_u32(sb);
+                        const uint32_t a0 = smem_u32(sa);
+                        const uint32_t a1 = a0 + G.a_bytes;
+                        uint32_t acc = 0;
+                        for (int t = 0; t < G.nkc / 2; ++t) {
+                            const int kc = 2 * t;
+                            const int u = kc / G.pw, qq = kc % G.pw;
+                            const uint32_t boff = qq * G.qpitch + u * 16;
+                            const uint64_t da0 = sdesc(a0 + kc * 128, 128, sbo_a);
+                            const uint64_t db0 = sdesc(sbu + boff, lbo_b, 128);
+                            mma_bf16(d, da0, db0, idesc, acc);
+                            acc = 1;
+                            if (kF32) {
+                                const uint64_t db1 = sdesc(sbu + G.plane_stage + boff, lbo_b, 128);
+                                const uint64_t da1 = sdesc(a1 + kc * 128, 128, sbo_a);
+                                mma_bf16(d, da0, db1, idesc, 1);
+                                mma_bf16(d, da1, db0, idesc, 1);
+                            }
+                        }
+                        mma_bf16(d, sdesc(an, 128, 256), sdesc(sbu + nplanes * G.plane_stage, 16, 128),
+                                 idesc, 1);
+                        mma_commit(BAR(k, kBarSEmpty + stage));
+                        mma_commit(BAR(k, kBarTFull + buf));
+                        if (c + 1 == T.nchunks) mma_commit(BAR(k, kBarAEmpty));
                     }
                 }
-#pragma unroll
-                for (int u4 = 0; u4 < 4; ++u4)
-                    if (dst[u4] >= 0) *reinterpret_cast<uint4*>(sb + dst[u4]) = val[u4];
-            }
-            uint8_t* nsb = sb + nplanes * G.plane_stage;
-            const int* nrm_i = static_cast<const int*>(J.nrm);
-            const float* nrm_f = static_cast<const float*>(J.nrm);
-            for (int t = pt; t < norm_items; t += kProducers) {
-                const int row = t % G.Rb, jl = t / G.Rb;
-                if (jl >= kc_here) continue;
-                uint16_t hi = 0, mid = 0, lo = 0;
-                if (row < T.NR) {
-                    const size_t ni = (size_t)(T.Y0 + row) * J.Wc + (T.X0 + jc0 + jl);
-                    const float w = kF32 ? nrm_f[ni] : (float)nrm_i[ni];
-                    split3(w, hi, mid, lo);
-                } else {
-                    hi = bf16_bits(1.0e18f);  // no real candidate: never selected
-                }
-                uint4 val;
-                if (kF32) {
-                    val = make_uint4(hi | (uint32_t(mid) << 16), lo | (uint32_t(hi) << 16),
-                                     mid | (uint32_t(lo) << 16), 0u);
-                } else {
-                    val = make_uint4(hi | (uint32_t(mid) << 16), lo, 0u, 0u);
-                }
-                *reinterpret_cast<uint4*>(nsb + (jl * G.Rb + row) * 16) = val;
-            }
-            fence_proxy_async();
-            mbar_arrive(bar_full + 8 * stage);
-            ++step;
-            if (++chunk[k] == T.nchunks) {
-                chunk[k] = 0;
-                ++turn[k];
-                const int t = slot_tile(cta, turn[k], k, NS, grid);
-                active[k] = t < P.total_tiles;
-                if (active[k]) ti[k] = tile_info(P, t);
+                ok = __shfl_sync(0xffffffffu, lok, 0) != 0;
+                if (!ok) break;
+                norm_pending[stage] = -1;
             }
         }
-    } else if (warp == kMmaWarp) {
-        // ------------------------------------------------------------ MMA issuer
+        // drain: copies in flight, then every MMA issued by this slot, before
+        // the shared memory and TMEM are released
         if (lane == 0) {
-            const uint32_t an = smem_u32(smem + G.off_an);
-            const uint32_t sbo_a = G.nkc * 128;
-            const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
-            int nchunks[NS], center[NS], NX[NS], chunk[NS], turn[NS], q[NS];
-            bool active[NS];
-            for (int k = 0; k < NS; ++k) {
-                chunk[k] = turn[k] = q[k] = 0;
-                const int t = slot_tile(cta, 0, k, NS, grid);
-                active[k] = t < P.total_tiles;
-                if (active[k]) {
-                    const TileInfo T = tile_info(P, t);
-                    nchunks[k] = T.nchunks; center[k] = T.center_chunk; NX[k] = T.NX;
-                }
-            }
-            int step = 0, next = 0;
-            while (true) {
-                int k = next;
-                if (!active[k]) k = NS - 1 - k;
-                if (!active[k]) break;
-                next = NS - 1 - k;
-                if (chunk[k] == 0 &&
-                    !mbar_wait(bar_afull + 8 * k, turn[k] & 1, abort_flag, 6))
-                    break;
-                const int buf = q[k] & 1, ub = q[k] >> 1;
-                if (ub > 0 &&
-                    !mbar_wait(bar_tempty + 8 * (2 * k + buf), (ub - 1) & 1, abort_flag, 2))
-                    break;
-                const int stage = step % kStages, use = step / kStages;
-                if (!mbar_wait(bar_full + 8 * stage, use & 1, abort_flag, 3)) break;
-                tc_fence_after();
-                const int jc0 = chunk_order(chunk[k], nchunks[k], center[k]) * G.kcols;
-                const int kc_here = min(G.kcols, NX[k] - jc0);
-                const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
-                const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
-                const uint32_t sb = smem_u32(smem + G.off_stage + stage * G.stage_bytes);
-                const uint32_t a0 = smem_u32(smem + G.off_a + k * G.a_bytes * nplanes);
-                const uint32_t a1 = a0 + G.a_bytes;
-                uint32_t acc = 0;
-                for (int t = 0; t < G.nkc / 2; ++t) {
-                    const int kc = 2 * t;
-                    const int u = kc / G.pw, qq = kc % G.pw;
-                    const uint32_t boff = qq * G.qpitch + u * 16;
-                    const uint64_t da0 = sdesc(a0 + kc * 128, 128, sbo_a);
-                    const uint64_t db0 = sdesc(sb + boff, lbo_b, 128);
-                    mma_bf16(d, da0, db0, idesc, acc);
-                    acc = 1;
-                    if (kF32) {
-                        const uint64_t db1 = sdesc(sb + G.plane_stage + boff, lbo_b, 128);
-                        const uint64_t da1 = sdesc(a1 + kc * 128, 128, sbo_a);
-                        mma_bf16(d, da0, db1, idesc, 1);
-                        mma_bf16(d, da1, db0, idesc, 1);
-                    }
-                }
-                const uint32_t nsb = sb + nplanes * G.plane_stage;
-                mma_bf16(d, sdesc(an, 128, 256), sdesc(nsb, 16, 128), idesc, 1);
-                mma_commit(bar_empty + 8 * stage);
-                mma_commit(bar_tfull + 8 * (2 * k + buf));
-                ++step;
-                ++q[k];
-                if (++chunk[k] == nchunks[k]) {
-                    mma_commit(bar_aempty + 8 * k);  // A region of slot k free once these finish
-                    chunk[k] = 0;
-                    ++turn[k];
-                    const int t = slot_tile(cta, turn[k], k, NS, grid);
-                    active[k] = t < P.total_tiles;
-                    if (active[k]) {
-                        const TileInfo T = tile_info(P, t);
-                        nchunks[k] = T.nchunks; center[k] = T.center_chunk; NX[k] = T.NX;
-                    }
-                }
-            }
-            // drain: wait for every MMA issued by this thread before TMEM is freed
-            mma_commit(bar_done);
-            const unsigned long long t0 = globaltimer();
-            while (!mbar_try_wait(bar_done, 0) && globaltimer() - t0 < kWaitNs) {
-            }
+            if (base_pending >= 0) mbar_drain(BAR(k, kBarBase), base_pending);
+            for (int i = 0; i < kMaxSt; ++i)
+                if (norm_pending[i] >= 0) mbar_drain(BAR(k, kBarNFull + i), norm_pending[i]);
+            mma_commit(BAR(k, kBarDone));
+            mbar_drain(BAR(k, kBarDone), 0);
         }
         __syncwarp();
     } else {
@@ -822,18 +843,24 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
         // the lane's threshold are appended with predicated stores; when any
         // lane's buffer nears full the warp merges in lock-step.
         const int k = warp >> 2, quarter = warp & 3;
+        uint8_t* slot = smem + G.off_slots + k * G.slot_bytes;
         unsigned long long* pend =
-            reinterpret_cast<unsigned long long*>(smem + G.off_buf) + threadIdx.x;
+            reinterpret_cast<unsigned long long*>(slot + G.off_buf) + (threadIdx.x & 127);
+        unsigned* pend32 = reinterpret_cast<unsigned*>(slot + G.off_buf) + (threadIdx.x & 127);
+        const unsigned kM = (1u << G.tbits) - 1u;   // window-index bits of a 32-bit key
+        const int ww = 2 * G.h + 1;
         Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + (threadIdx.x & 127), G.HL};
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        int qc = 0;  // slot-local chunk counter (TMEM buffer phase)
+        int qc = 0;  // slot-local chunk counter (accumulator phase)
         for (int turn = 0; !*abort_flag; ++turn) {
             const int tile = slot_tile(cta, turn, k, NS, grid);
             if (tile >= P.total_tiles) break;
             const TileInfo T = tile_info(P, tile);
             const TcJob& J = *T.job;
             RegTopK<LC == 0 ? 1 : LC> reg;
-            reg.init(G.HL);
+            RegTopK<32, unsigned> reg32;
+            if constexpr (K32) reg32.init(G.HL);
+            else reg.init(G.HL);
             if constexpr (LC == 0) {
                 for (int i = 0; i < G.HL; ++i) heap.h[i * 128] = kEmpty;
             }
@@ -850,7 +877,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             int cnt = 0;
             for (int c = 0; c < T.nchunks; ++c, ++qc) {
                 const int buf = qc & 1, ub = qc >> 1;
-                if (!mbar_wait(bar_tfull + 8 * (2 * k + buf), ub & 1, abort_flag, 4)) break;
+                if (!mbar_wait(BAR(k, kBarTFull + buf), ub & 1, abort_flag, 4)) break;
                 tc_fence_after();
                 const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
                 const int kc_here = min(G.kcols, T.NX - jc0);
@@ -868,40 +895,58 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                         float w[16];
                         tmem_ld_blocks<1>(colbase + 16 * bb, w);
                         const int b = b0 + bb;
-                        // this lane's valid rows of block b: [i0, i1] (may be empty)
-                        const int i0 = lo - 16 * b, i1 = xok ? hi - 16 * b : -1;
-                        const float ninf = -__int_as_float(0x7f800000);
-                        float m = ninf;
+                        // this lane's valid rows of block b: [max(i0, 0), min(i1, 15)]
+                        const int i0 = max(lo - 16 * b, 0), i1 = min(hi - 16 * b, 15);
+                        const unsigned rows = (xok && i1 >= i0)
+                                                  ? ((0xffffu >> (15 - i1)) & (0xffffu << i0))
+                                                  : 0u;
+                        // rows at or above the threshold, as a bit mask
+                        unsigned bits = 0;
 #pragma unroll
-                        for (int i = 0; i < 16; i += 2) {
-                            const float a = (i >= i0 && i <= i1) ? w[i] : ninf;
-                            const float c2 = (i + 1 >= i0 && i + 1 <= i1) ? w[i + 1] : ninf;
-                            m = max3(m, a, c2);
-                        }
-                        const bool hit = m >= thr;
-                        if (!__any_sync(0xffffffffu, hit)) continue;  // next block
-                        if (hit) {
-                            const int ybase = T.Y0 + 16 * b;
+                        for (int i = 0; i < 16; ++i) bits |= (w[i] >= thr ? 1u : 0u) << i;
+                        bits &= rows;
+                        if (bits) {
+                            if constexpr (K32) {
+                                // window index of row 16b + i: (row - yr + h) * ww + (xc - xr + h)
+                                const unsigned base =
+                                    (unsigned)((T.Y0 + 16 * b - yr + G.h) * ww + (xc - xr + G.h));
+                                do {
+                                    const int i = __ffs(bits) - 1;
+                                    bits &= bits - 1;
+                                    float wi = w[0];
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                if (i >= i0 && i <= i1 && w[i] >= thr) {
-                                    pend[cnt * kEpi] =
-                                        ((unsigned long long)__float_as_uint(w[i]) << 32) |
-                                        (unsigned)((ybase + i) * J.W + xc);
+                                    for (int t = 1; t < 16; ++t) wi = i == t ? w[t] : wi;
+                                    pend32[cnt * 128] = (~orderable(wi) & ~kM) | (base + (unsigned)(i * ww));
                                     ++cnt;
-                                }
+                                } while (bits);
+                            } else {
+                                const unsigned base = (unsigned)((T.Y0 + 16 * b) * J.W + xc);
+                                do {
+                                    const int i = __ffs(bits) - 1;
+                                    bits &= bits - 1;
+                                    float wi = w[0];
+#pragma unroll
+                                    for (int t = 1; t < 16; ++t) wi = i == t ? w[t] : wi;
+                                    pend[cnt * 128] = ((unsigned long long)__float_as_uint(wi) << 32) |
+                                                      (base + (unsigned)(i * J.W));
+                                    ++cnt;
+                                } while (bits);
                             }
                         }
                         // keep room for the next block's appends
-                        if (__any_sync(0xffffffffu, cnt > kBuf - 16))
-                            merge_pending<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+                        if (__any_sync(0xffffffffu, cnt > G.kbuf - 16)) {
+                            if constexpr (K32) merge_pending32(pend32, cnt, thr, reg32, kM);
+                            else merge_pending<LC, kF32, 128>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
+                        }
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(bar_tempty + 8 * (2 * k + buf));
+                mbar_arrive(BAR(k, kBarTEmpty + buf));
             }
-            if (__any_sync(0xffffffffu, cnt > 0))
-                reg = final_merge<LC, kF32, kEpi>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
+            if (__any_sync(0xffffffffu, cnt > 0)) {
+                if constexpr (K32) reg32 = final_merge32(pend32, cnt, reg32, kM);
+                else reg = final_merge<LC, kF32, 128>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
+            }
             // ---- write results
             if (lane_ok && !*abort_flag) {
                 const size_t ref = (size_t)ry * J.n_rx + rx;
@@ -922,7 +967,24 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                             key == kEmpty ? 0x7fffffff : (int32_t)(unsigned)(key >> 32);
                     }
                 };
-                if constexpr (LC > 0) {
+                if constexpr (K32) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i < nout) {
+                            const unsigned key = reg32.a[i];
+                            int32_t off = -1;
+                            float v = -__int_as_float(0x7f800000);
+                            if (key != ~0u) {
+                                const int li = (int)(key & kM);
+                                const int dy = li / ww - G.h, dx = li % ww - G.h;
+                                off = (yr + dy) * J.W + (xr + dx);
+                                v = from_orderable(~(key & ~kM));  // upper end of the key's bucket
+                            }
+                            J.pool_idx[ref * G.HL + i] = off;
+                            J.pool_score[ref * G.HL + i] = v;
+                        }
+                    }
+                } else if constexpr (LC > 0) {
 #pragma unroll
                     for (int i = 0; i < LC; ++i)
                         if (i < nout) emit(i, reg.a[i]);
@@ -935,7 +997,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == kEpiWarps) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
@@ -943,57 +1005,88 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 }
 
 // Class geometry for a job shape: lane mapping, strips, slots, shared memory.
+// Preference: two tiles in flight (when the list lives in registers), then
+// the mapping with the least MMA work, then the largest append buffer and
+// the deepest stage ring that fit the shared memory.
 bool make_tc_geom(const Geom& g, TcGeom& t) {
+    t = TcGeom{};
     t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
     t.pw = g.pw; t.p_eff = g.p_eff; t.nkc = g.p_eff * g.pw;
     t.f32 = g.dtype == kF32;
     t.HL = t.f32 ? g.L : g.K;
-    // two tiles in flight when the list lives in registers and a strip fits
-    // a 128-column accumulator; one otherwise
+    const int nplanes = t.f32 ? 2 : 1;
+    // float32 lists in registers use 32-bit keys when the window index fits
+    // 12 bits (window <= 63): 2^-11 relative rounding of the pool scores
+    t.tbits = 0;
+    if (t.f32 && t.HL <= 32) {
+        const int ww = 2 * g.h + 1;
+        int b = 1;
+        while ((1 << b) < ww * ww) ++b;
+        if (b <= 12) t.tbits = b;
+    }
+    // lane -> reference mapping: rr reference rows x rc columns per warp, a
+    // wgy x wgx grid of 4 warps
+    static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
     for (int ns = 2; ns >= 1; --ns) {
         if (ns == 2 && t.HL > 32) continue;
         const int bufcols = kTmemCols / (2 * ns);
-        // lane -> reference mapping: rr reference rows x rc columns per warp,
-        // a wgy x wgx grid of 4 warps; least MMA work (union columns x strip
-        // rows), ties to the earlier (narrower) entry
-        static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
-        long long best = -1;
-        for (const auto& mp : kMaps) {
-            const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
-            const int ty = wgy * rr, tx = wgx * rc;
-            const int nr_max = (ty - 1) * g.s + 2 * g.h + 1;
-            const int nx_max = (tx - 1) * g.s + 2 * g.h + 1;
-            const int rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
-            if (rb > bufcols) continue;
-            const long long work = (long long)nx_max * rb;
-            if (best < 0 || work < best) {
-                best = work;
-                t.rr = rr; t.rc = rc; t.wgx = wgx; t.ty = ty; t.tx = tx; t.Rb = rb;
-            }
+        bool found = false;
+        long long best = 0;
+        TcGeom bestc{};
+        for (const auto& mp : kMaps)
+            for (int kbuf = 32; kbuf >= 16; kbuf -= 16)
+                for (int nst = kMaxSt; nst >= 2; --nst) {
+                    TcGeom c = t;
+                    const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
+                    c.rr = rr; c.rc = rc; c.wgx = wgx; c.ty = wgy * rr; c.tx = wgx * rc;
+                    const int nr_max = (c.ty - 1) * g.s + 2 * g.h + 1;
+                    const int nx_max = (c.tx - 1) * g.s + 2 * g.h + 1;
+                    c.Rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
+                    if (c.Rb > bufcols) continue;
+                    // staged row: alignment slack + every candidate column's patch row;
+                    // an odd 16-byte chunk count keeps 16-byte row reads conflict-free
+                    c.nc_box = ((7 + (nx_max - 1) * g.Cp + 8 * g.pw + 7) / 8) | 1;
+                    if (c.nc_box > 255) continue;
+                    c.nslots = ns;
+                    c.bufcols = bufcols;
+                    c.nst = nst;
+                    c.kbuf = kbuf;
+                    c.kcols = bufcols / c.Rb;
+                    c.base_pitch = c.nc_box * 16;
+                    c.base_bytes = c.Rb * c.base_pitch;
+                    c.qpitch = (c.kcols * c.Rb + g.p_eff + 16) * 16;
+                    c.plane_stage = c.pw * c.qpitch;
+                    c.stage_bytes = (nplanes * c.plane_stage + c.kcols * c.Rb * 16 + 127) / 128 * 128;
+                    c.a_bytes = 128 * c.nkc * 16;
+                    // one slot: staged tile, A, stages, append buffers
+                    int off = 0;
+                    c.off_base = off; off += (nplanes * c.base_bytes + 1023) / 1024 * 1024;
+                    c.off_a = off; off += nplanes * c.a_bytes;
+                    c.off_stage = off; off += nst * c.stage_bytes;
+                    c.off_buf = off; off += 128 * kbuf * 8;
+                    c.slot_bytes = (off + 1023) / 1024 * 1024;
+                    off = 0;
+                    c.off_slots = off; off += ns * c.slot_bytes;
+                    c.off_an = off; off += 128 * 2 * 16;
+                    c.off_heap = off; off += c.HL > 32 ? 128 * c.HL * 8 : 0;
+                    c.off_bar = off; off += ns * kBarsPerSlot * 8 + 16;
+                    c.smem_total = (off + 1023) / 1024 * 1024;
+                    if (c.smem_total > kSmemLimit) continue;
+                    // least MMA work (union columns x strip rows); among equals the
+                    // first fit: the larger append buffer, then deeper stages
+                    const long long work = (long long)nx_max * c.Rb;
+                    if (!found || work < best) {
+                        found = true;
+                        best = work;
+                        bestc = c;
+                    }
+                }
+        if (found) {
+            t = bestc;
+            return true;
         }
-        if (best < 0) continue;
-        t.nslots = ns;
-        t.bufcols = bufcols;
-        break;
     }
-    if (t.Rb <= 0 || t.Rb > kBufCols) return false;
-    t.kcols = t.bufcols / t.Rb;
-    const int strip_rows = t.kcols * t.Rb + g.p_eff + 16;
-    t.qpitch = strip_rows * 16;
-    t.plane_stage = t.pw * t.qpitch;
-    t.ns_bytes = (t.kcols * t.Rb + 16) * 16;
-    const int nplanes = t.f32 ? 2 : 1;
-    t.stage_bytes = (nplanes * t.plane_stage + t.ns_bytes + 127) / 128 * 128;
-    int off = 0;
-    t.a_bytes = 128 * t.nkc * 16;
-    t.off_a = off; off += t.nslots * nplanes * t.a_bytes;
-    t.off_an = off; off += 128 * 2 * 16;
-    t.off_stage = off; off += kStages * t.stage_bytes;
-    t.off_heap = off; off += t.HL > 32 ? 128 * t.HL * 8 : 0;
-    t.off_buf = off; off += 4 * t.nslots * 32 * kBuf * 8;
-    t.off_bar = off; off += (2 * kStages + 6 * t.nslots + 1) * 8 + 16;
-    t.smem_total = (off + 1023) / 1024 * 1024;
-    return t.smem_total <= kSmemLimit;
+    return false;
 }
 
 int num_sms() {
@@ -1007,36 +1100,73 @@ int num_sms() {
     return n;
 }
 
-TcJob make_job(const Geom& g, const TcGeom& t, const TcArgs& a, int tile_begin) {
-    TcJob j{};
-    j.plane0 = a.plane0;
-    j.plane1 = a.plane1;
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Plane as a 3-D tensor {8 elements, 16-byte chunks of a row, rows}; the box
+// is one staged tile: nc_box chunks x Rb rows.  Out-of-range boxes read zeros.
+bool encode_plane(CUtensorMap* m, const uint16_t* plane, const Geom& g, const TcGeom& t) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || !plane) return false;
+    const cuuint64_t dims[3] = {8, (cuuint64_t)g.plane_pitch / 8, (cuuint64_t)g.plane_rows};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)g.plane_pitch * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)t.nc_box, (cuuint32_t)t.Rb};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(plane), dims, strides,
+              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_job(TcJob& j, const Geom& g, const TcGeom& t, const TcArgs& a, int tile_begin) {
+    j = TcJob{};
+    if (!encode_plane(&j.map[0], a.plane0, g, t)) return false;
+    if (t.f32 && !encode_plane(&j.map[1], a.plane1, g, t)) return false;
+    j.nsp = a.nsp;
     j.nrm = a.nrm;
     j.out_idx = a.out_idx;
     j.out_dist = a.out_dist;
     j.pool_idx = a.pool_idx;
     j.pool_score = a.pool_score;
     j.H = g.H; j.W = g.W; j.n_ry = g.n_ry; j.n_rx = g.n_rx; j.Hc = g.Hc; j.Wc = g.Wc;
-    j.plane_pitch = g.plane_pitch;
     j.tiles_x = (g.n_rx + t.tx - 1) / t.tx;
     j.tile_begin = tile_begin;
-    return j;
+    return true;
 }
 
 cudaError_t launch_params(TcParams& P, cudaStream_t st) {
     const TcGeom& T = P.g;
+    // at least 116 KB so that one CTA (one 512-column TMEM allocation) runs per SM
     const int smem = T.smem_total < 116 * 1024 ? 116 * 1024 : T.smem_total;
     void (*kern)(TcParams);
     int threads;
     if (T.nslots == 2) {
-        threads = cta_threads<8>();
-        if (T.f32) kern = tc_match_kernel<32, true, 2>;
-        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 2> : tc_match_kernel<32, false, 2>;
+        threads = cta_threads(2);
+        if (T.f32) kern = T.tbits ? tc_match_kernel<32, true, 2, true> : tc_match_kernel<32, true, 2, false>;
+        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 2, false> : tc_match_kernel<32, false, 2, false>;
     } else {
-        threads = cta_threads<4>();
-        if (T.f32) kern = T.HL <= 32 ? tc_match_kernel<32, true, 1> : tc_match_kernel<0, true, 1>;
-        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 1>
-                  : T.HL <= 32 ? tc_match_kernel<32, false, 1> : tc_match_kernel<0, false, 1>;
+        threads = cta_threads(1);
+        if (T.f32) kern = T.HL > 32 ? tc_match_kernel<0, true, 1, false>
+                        : T.tbits ? tc_match_kernel<32, true, 1, true> : tc_match_kernel<32, true, 1, false>;
+        else kern = T.HL <= 16 ? tc_match_kernel<16, false, 1, false>
+                  : T.HL <= 32 ? tc_match_kernel<32, false, 1, false> : tc_match_kernel<0, false, 1, false>;
     }
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int per = T.nslots;
@@ -1054,6 +1184,11 @@ bool tc_supported(const Geom& g) {
     return make_tc_geom(g, t);
 }
 
+int tc_score_bits(const Geom& g) {
+    TcGeom t{};
+    return make_tc_geom(g, t) ? t.tbits : 0;
+}
+
 // Jobs that can share one persistent launch (same class geometry).
 bool tc_same_class(const Geom& a, const Geom& b) {
     return a.dtype == b.dtype && a.Cp == b.Cp && a.p == b.p && a.h == b.h && a.s == b.s &&
@@ -1064,8 +1199,10 @@ cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {
     return launch_tc_batch(&g, &a, 1, st);
 }
 
-cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st) {
+cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st,
+                            int* nlaunch) {
     int i = 0;
+    if (nlaunch) *nlaunch = 0;
     while (i < n) {
         static thread_local TcParams P;
         P = TcParams{};
@@ -1073,7 +1210,7 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         P.status = as[i].status;
         int tiles = 0, nj = 0;
         while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj])) {
-            P.jobs[nj] = make_job(gs[i], P.g, as[i], tiles);
+            if (!make_job(P.jobs[nj], gs[i], P.g, as[i], tiles)) return cudaErrorInvalidValue;
             tiles += P.jobs[nj].tiles_x * ((gs[i].n_ry + P.g.ty - 1) / P.g.ty);
             ++nj;
             ++i;
@@ -1082,6 +1219,7 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         P.total_tiles = tiles;
         cudaError_t e = launch_params(P, st);
         if (e != cudaSuccess) return e;
+        if (nlaunch) ++*nlaunch;
     }
     return cudaSuccess;
 }
