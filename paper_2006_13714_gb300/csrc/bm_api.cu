@@ -205,12 +205,9 @@ cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch, const int
     return e;
 }
 
-// First kernels of a tensor-core job on st (workspace ws of job_ws_bytes):
-// status reset, centring offset, bf16 planes, box filter; fills the
-// tensor-core arguments a.
-int prep_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStream_t st,
-             TcArgs& a) {
-    cudaError_t e;
+// Workspace pointers of a tensor-core job: preparation job and tensor-core
+// arguments.
+void job_views(const Geom& g, const bm_request& r, void* ws, PrepJob& pj, TcArgs& a) {
     WsLayout l = ws_layout(g);
     char* b = static_cast<char*>(ws);
     uint16_t* p0 = reinterpret_cast<uint16_t*>(b + l.plane0);
@@ -219,17 +216,8 @@ int prep_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStre
     uint16_t* nsp = reinterpret_cast<uint16_t*>(b + l.nsp);
     int* status = reinterpret_cast<int*>(b + l.status);
     float* center = reinterpret_cast<float*>(b + l.status + 16);
-    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st)) != cudaSuccess)
-        return cuda_fail(e, "status reset");
-    if ((e = timed(ctx, BM_STAGE_PLANES, st,
-                   [&] { return launch_center(g, r.img, center, st); })) != cudaSuccess)
-        return cuda_fail(e, "centre kernel launch");
-    if ((e = timed(ctx, BM_STAGE_PLANES, st,
-                   [&] { return launch_planes(g, r.img, center, p0, p1, st); })) != cudaSuccess)
-        return cuda_fail(e, "plane kernel launch");
-    if ((e = timed(ctx, BM_STAGE_BOX, st,
-                   [&] { return launch_boxfilter(g, r.img, center, nrm, nsp, st); })) != cudaSuccess)
-        return cuda_fail(e, "box filter launch");
+    pj = make_prep_job(g, r.img, center, p0, p1, nrm, nsp);
+    pj.status = status;
     a = TcArgs{};
     a.plane0 = p0;
     a.plane1 = p1;
@@ -243,6 +231,21 @@ int prep_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaStre
         a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
         a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
     }
+}
+
+// Preparation kernels of n tensor-core jobs (status reset + centring offset,
+// bf16 planes, box filter): one launch per stage.
+int prep_jobs(bm_ctx* ctx, const PrepJob* pj, int n, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = timed(ctx, BM_STAGE_PLANES, st,
+                   [&] { return launch_center_batch(pj, n, st); })) != cudaSuccess)
+        return cuda_fail(e, "centre kernel launch");
+    if ((e = timed(ctx, BM_STAGE_PLANES, st,
+                   [&] { return launch_planes_batch(pj, n, st); })) != cudaSuccess)
+        return cuda_fail(e, "plane kernel launch");
+    if ((e = timed(ctx, BM_STAGE_BOX, st,
+                   [&] { return launch_box_batch(pj, n, st); })) != cudaSuccess)
+        return cuda_fail(e, "box filter launch");
     return BM_OK;
 }
 
@@ -268,7 +271,9 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
         return BM_OK;
     }
     TcArgs a;
-    int rc = prep_job(ctx, g, r, ws, st, a);
+    PrepJob pj;
+    job_views(g, r, ws, pj, a);
+    int rc = prep_jobs(ctx, &pj, 1, st);
     if (rc != BM_OK) return rc;
     if ((e = timed(ctx, BM_STAGE_TC, st, [&] { return launch_tc(g, a, st); })) != cudaSuccess)
         return cuda_fail(e, "tensor-core kernel launch");
@@ -560,17 +565,21 @@ int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream)
     // share a launch), then the float32 re-ranks
     std::vector<int> tc_ids;
     std::vector<TcArgs> args(n);
+    std::vector<PrepJob> pjs;
     for (int i = 0; i < n; ++i) {
-        int rc;
         if (!use_tc(ctx, gs[i])) {
-            rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, st);
+            int rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, st);
+            if (rc != BM_OK) return rc;
         } else {
-            rc = prep_job(ctx, gs[i], reqs[i], static_cast<char*>(ws) + offs[i], st, args[i]);
+            PrepJob pj;
+            job_views(gs[i], reqs[i], static_cast<char*>(ws) + offs[i], pj, args[i]);
+            pjs.push_back(pj);
             tc_ids.push_back(i);
         }
-        if (rc != BM_OK) return rc;
     }
     if (!tc_ids.empty()) {
+        int rc = prep_jobs(ctx, pjs.data(), (int)pjs.size(), st);
+        if (rc != BM_OK) return rc;
         auto key = [&](int i) {
             const Geom& g = gs[i];
             return std::make_tuple(g.dtype, g.Cp, g.p, g.h, g.s, g.K, g.L);
@@ -588,9 +597,23 @@ int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream)
         }, &nl);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
         ctx->tc_jobs += tc_ids.size();
+        std::vector<Geom> rg;
+        std::vector<RerankArgs> ra;
         for (int i : tc_ids) {
-            int rc = finish_job(ctx, gs[i], reqs[i], args[i], st);
-            if (rc != BM_OK) return rc;
+            if (gs[i].dtype != kF32) continue;
+            rg.push_back(gs[i]);
+            ra.push_back(RerankArgs{static_cast<const float*>(reqs[i].img),
+                                    static_cast<const float*>(args[i].nrm), args[i].pool_idx,
+                                    args[i].pool_score, reqs[i].out_idx,
+                                    static_cast<float*>(reqs[i].out_dist)});
+        }
+        if (!rg.empty()) {
+            int nr = 0;
+            e = timed(ctx, BM_STAGE_RERANK, st, [&] {
+                return launch_rerank_batch(rg.data(), ra.data(), (int)rg.size(), ctx->d_counters,
+                                           st, &nr);
+            }, &nr);
+            if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
         }
     }
     for (int i = 0; i < n; ++i) {

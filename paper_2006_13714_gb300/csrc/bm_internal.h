@@ -44,6 +44,25 @@ size_t nsp_bytes(const Geom& g);         // split candidate norms (16 bytes each
 
 // ---- kernels (each launcher returns cudaGetLastError()) ----
 
+// One image's preparation (centre, planes, box filter) inside a batch.
+struct PrepJob {
+    const void* img;
+    float* center;            // centring offset (written by the centre kernel)
+    int* status;              // nullable: device error word, zeroed by the centre kernel
+    uint16_t* plane0;         // bf16 planes
+    uint16_t* plane1;
+    void* nrm;                // norms [Hc][Wc]
+    uint16_t* nsp;            // nullable: split norms [Wc][Hc][8]
+    int H, W, C, Cp, p, Hc, Wc, plane_pitch, plane_rows, dtype;
+};
+PrepJob make_prep_job(const Geom& g, const void* img, float* center, uint16_t* plane0,
+                      uint16_t* plane1, void* nrm, uint16_t* nsp);
+// Batched forms (one launch per stage for up to 64 jobs; the centre must
+// precede the planes and the box filter).
+cudaError_t launch_center_batch(const PrepJob* jobs, int n, cudaStream_t st);
+cudaError_t launch_planes_batch(const PrepJob* jobs, int n, cudaStream_t st);
+cudaError_t launch_box_batch(const PrepJob* jobs, int n, cudaStream_t st);
+
 // Centring offset c of the operands (distances are shift-invariant):
 // uint8 -> 128 (constant, nothing written but a zero), float32 -> a sampled
 // image mean written to *center.
@@ -98,6 +117,21 @@ cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
                           const int32_t* pool_idx, const float* pool_score,
                           int32_t* out_idx, float* out_dist, unsigned long long* counters,
                           cudaStream_t st);
+struct RerankArgs {
+    const float* img;
+    const float* nrm;
+    const int32_t* pool_idx;
+    const float* pool_score;
+    int32_t* out_idx;
+    float* out_dist;
+};
+// Jobs that can share one re-rank launch.
+bool rerank_same_class(const Geom& a, const Geom& b);
+// Several float32 jobs; consecutive jobs of one class share a launch (up to
+// 64 each); *nlaunch (nullable) = kernel launches made.
+cudaError_t launch_rerank_batch(const Geom* gs, const RerankArgs* as, int n,
+                                unsigned long long* counters, cudaStream_t st,
+                                int* nlaunch = nullptr);
 
 // Sets the calling thread's bm_last_error message and returns code.
 int set_error(int code, const char* msg);

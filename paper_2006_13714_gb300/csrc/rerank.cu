@@ -3,7 +3,7 @@
 // The tensor-core pass leaves, per reference r, a pool of the L largest
 // v_j = b~_j + eps n_j (b~ the split-bf16 estimate of Theorem 1's score
 // b_j = C_r(j) - 0.5 n_j of the centred patches, n_j = ||X_j - c||^2,
-// eps = 2^-14), in any order.  The identity d = ||X_r||^2 - 2 b (Lemma 2)
+// eps = 2^-14), best first.  The identity d = ||X_r||^2 - 2 b (Lemma 2)
 // loses precision to cancellation in proportion to n_r + n_j, not to d, so
 // the final distances are recomputed here directly:
 //
@@ -24,8 +24,14 @@
 //      order there follows the FP64 values.
 //   4. Counter: band members whose identity estimate misses the direct
 //      distance by more than the bound (expected 0).
-// One warp per reference; every ranking uses 64-bit integer keys (FP64 is
-// slow on this part and is kept to the rare boundary ties).
+//
+// Layout of the work: one block per tile of TRY x TRX references of one
+// image (a table of images per launch).  The block first stages the image
+// region its references' windows cover, and the norms there, in shared
+// memory, so every distance reads shared memory.  One warp per reference;
+// every ranking uses 64-bit integer keys (FP64 is slow on this part and is
+// kept to the rare boundary ties).  Shapes whose region does not fit run
+// the same steps on global memory, one image per launch.
 #include "bm_internal.h"
 
 #include <climits>
@@ -34,45 +40,69 @@ namespace bm {
 namespace {
 
 constexpr float kEps = 6.103515625e-05f;  // 2^-14, same constant as the tensor-core pass
-constexpr int kWarps = 4;
 constexpr int kFbSlots = (kMaxK + 1 + 31) / 32;
 constexpr unsigned long long kNone = ~0ull;
+constexpr int kTileWarps = 8;
+constexpr int kMaxRerankJobs = 64;
+constexpr int kTileSmemLimit = 160 * 1024;
 
-struct RerankParams {
+struct RerankJob {
     const float* img;
     const float* nrm;
     const int32_t* pool_idx;
     const float* pool_score;
     int32_t* out_idx;
     float* out_dist;
-    unsigned long long* counters;  // [0] overflow, [1] fp64 rechecks, [2] bound violations
-    int H, W, C, p, h, s, K, L, n_ry, n_rx, Wc, nR;
-    float round_rel;  // pool-score rounding, relative: 2^(tbits - 23) (0: exact scores)
+    int H, W, n_ry, n_rx, Hc, Wc;
+    int tiles_x, tile_begin;
 };
 
-__device__ __forceinline__ float direct_f32(const RerankParams& P, const float* ref, int yc, int xc) {
-    const int pc = P.p * P.C;
+struct RerankParams {
+    int C, p, h, s, K, L;
+    float round_rel;  // pool-score rounding, relative: 2^(tbits - 23) (0: exact scores)
+    float gamma;      // FP32 relative error bound of a direct distance
+    int TRY, TRX;     // references per tile (rows, columns)
+    int img_cap;      // shared-memory image region capacity (floats); norms follow
+    unsigned long long* counters;  // [0] overflow, [1] fp64 rechecks, [2] bound violations
+    int njobs, total_tiles;
+    RerankJob jobs[kMaxRerankJobs];
+};
+
+// Pixel source: a region of the image (shared memory) or the whole image;
+// element (y, x, c) at base + (y - y0) * pitch + (x - x0) * C + c.
+struct Pix {
+    const float* base;
+    int y0, x0, pitch, C;
+    __device__ __forceinline__ const float* at(int y, int x) const {
+        return base + (size_t)(y - y0) * pitch + (size_t)(x - x0) * C;
+    }
+};
+
+// (X_r - X_j)^2 summed row by row, elements in order (the reference's rows
+// at ref + u * pitch).
+__device__ __forceinline__ float direct_f32(const Pix& X, int p, int C, const float* ref, int yc, int xc) {
+    const int pc = p * C;
     float acc = 0.f;
-    for (int u = 0; u < P.p; ++u) {
-        const float* crow = P.img + ((size_t)(yc + u) * P.W + xc) * P.C;
-        const float* rrow = ref + u * pc;
+    for (int u = 0; u < p; ++u) {
+        const float* crow = X.at(yc + u, xc);
+        const float* rrow = ref + (size_t)u * X.pitch;
 #pragma unroll 8
         for (int e = 0; e < pc; ++e) {
-            const float d = rrow[e] - __ldg(crow + e);
+            const float d = rrow[e] - crow[e];
             acc = fmaf(d, d, acc);
         }
     }
     return acc;
 }
 
-__device__ __forceinline__ double direct_f64(const RerankParams& P, const float* ref, int yc, int xc) {
-    const int pc = P.p * P.C;
+__device__ __forceinline__ double direct_f64(const Pix& X, int p, int C, const float* ref, int yc, int xc) {
+    const int pc = p * C;
     double acc = 0.0;
-    for (int u = 0; u < P.p; ++u) {
-        const float* crow = P.img + ((size_t)(yc + u) * P.W + xc) * P.C;
-        const float* rrow = ref + u * pc;
+    for (int u = 0; u < p; ++u) {
+        const float* crow = X.at(yc + u, xc);
+        const float* rrow = ref + (size_t)u * X.pitch;
         for (int e = 0; e < pc; ++e) {
-            const double d = (double)rrow[e] - (double)__ldg(crow + e);
+            const double d = (double)rrow[e] - (double)crow[e];
             acc = fma(d, d, acc);
         }
     }
@@ -94,18 +124,13 @@ __device__ __forceinline__ void warp_rank(const unsigned long long (&key)[S], in
     }
 }
 
-__device__ __forceinline__ unsigned orderable(float f) {
-    const unsigned b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
 // Final selection: members carry key (float(d32) bits << 32 | offset);
 // non-members carry kNone.  FP64 refinement at the K-th boundary, then write
 // ranks < K (and the padding).
 template <int S>
-__device__ void select_and_write(const RerankParams& P, const float* ref,
-                                 const unsigned long long (&key)[S], int nb, int lane, size_t r,
-                                 float gamma) {
+__device__ void select_and_write(const RerankParams& P, const RerankJob& J, const Pix& X,
+                                 const float* ref, const unsigned long long (&key)[S], int nb,
+                                 int lane, size_t r) {
     int rank[S];
     warp_rank(key, rank);
     double d64[S];
@@ -127,7 +152,7 @@ __device__ void select_and_write(const RerankParams& P, const float* ref,
             din = fmaxf(din, __shfl_xor_sync(0xffffffffu, din, o));
             dout = fmaxf(dout, __shfl_xor_sync(0xffffffffu, dout, o));
         }
-        const float tol = gamma * (din + dout);
+        const float tol = P.gamma * (din + dout);
         if (dout - din <= tol) {
             // boundary members: FP64 distances decide their order
             int nrec = 0;
@@ -136,7 +161,7 @@ __device__ void select_and_write(const RerankParams& P, const float* ref,
                 const float d = __uint_as_float((unsigned)(key[i] >> 32));
                 if (key[i] != kNone && d >= din - 2.f * tol && d <= dout + 2.f * tol) {
                     const int off = (int)(unsigned)(key[i] & 0xffffffffu);
-                    d64[i] = direct_f64(P, ref, off / P.W, off % P.W);
+                    d64[i] = direct_f64(X, P.p, P.C, ref, off / J.W, off % J.W);
                     refined[i] = true;
                     ++nrec;
                 }
@@ -178,37 +203,29 @@ __device__ void select_and_write(const RerankParams& P, const float* ref,
 #pragma unroll
     for (int i = 0; i < S; ++i) {
         if (key[i] != kNone && rank[i] < P.K) {
-            P.out_idx[r * P.K + rank[i]] = (int32_t)(unsigned)(key[i] & 0xffffffffu);
-            P.out_dist[r * P.K + rank[i]] =
+            J.out_idx[r * P.K + rank[i]] = (int32_t)(unsigned)(key[i] & 0xffffffffu);
+            J.out_dist[r * P.K + rank[i]] =
                 refined[i] ? (float)d64[i] : __uint_as_float((unsigned)(key[i] >> 32));
         }
     }
     for (int k = nb + lane; k < P.K; k += 32) {
-        P.out_idx[r * P.K + k] = -1;
-        P.out_dist[r * P.K + k] = __int_as_float(0x7f800000);
+        J.out_idx[r * P.K + k] = -1;
+        J.out_dist[r * P.K + k] = __int_as_float(0x7f800000);
     }
 }
 
+// The steps of the file header for reference (ry, rx) of job J.  X holds
+// every pixel of the patches of its window, N (C = 1) every norm of its
+// window; list: kFbSlots * 32 words of shared memory for the overflow path.
 template <int S>
-__global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_constant__ RerankParams P) {
-    __shared__ float ref_s[kWarps][kMaxPatchElems];
-    __shared__ unsigned long long list_s[kWarps][kFbSlots * 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t r = (size_t)blockIdx.x * kWarps + warp;
-    if (r >= (size_t)P.nR) return;
-    const int ry = (int)(r / P.n_rx), rx = (int)(r % P.n_rx);
+__device__ void rerank_ref(const RerankParams& P, const RerankJob& J, const Pix& X, const Pix& N,
+                           int ry, int rx, int lane, unsigned long long* list) {
+    const size_t r = (size_t)ry * J.n_rx + rx;
     const int yr = ry * P.s, xr = rx * P.s;
-    const int pc = P.p * P.C;
-    for (int e = lane; e < P.p * pc; e += 32) {
-        const int u = e / pc, k = e % pc;
-        ref_s[warp][e] = P.img[((size_t)(yr + u) * P.W + xr) * P.C + k];
-    }
-    __syncwarp();
-    const float* ref = ref_s[warp];
-    const float nr = P.nrm[(size_t)yr * P.Wc + xr];
-    const float gamma = (float)(pc * P.p + 3) * 5.9604645e-08f;  // (n + 3) 2^-24
+    const float* ref = X.at(yr, xr);  // reference rows at ref + u * X.pitch
+    const float nr = *N.at(yr, xr);
 
-    // ---- load the pool (any order; empty slots have offset -1)
+    // ---- load the pool (best first; empty slots have offset -1)
     float v[S], nc[S];
     int off[S];
     int npool = 0;
@@ -219,35 +236,30 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         off[i] = -1;
         nc[i] = 0.f;
         if (k < P.L) {
-            off[i] = P.pool_idx[r * P.L + k];
+            off[i] = J.pool_idx[r * P.L + k];
             if (off[i] >= 0) {
-                v[i] = P.pool_score[r * P.L + k];
-                nc[i] = P.nrm[(size_t)(off[i] / P.W) * P.Wc + (off[i] % P.W)];
+                v[i] = J.pool_score[r * P.L + k];
+                nc[i] = *N.at(off[i] / J.W, off[i] % J.W);
                 ++npool;
             }
         }
     }
     for (int o = 16; o > 0; o >>= 1) npool += __shfl_xor_sync(0xffffffffu, npool, o);
 
-    // ---- band: entries with v >= T' (see the file header)
+    // ---- band: entries with v >= tb (see the file header); the pool is
+    // sorted, so the K-th largest score is entry K-1
     bool member[S];
 #pragma unroll
     for (int i = 0; i < S; ++i) member[i] = off[i] >= 0;
     int nb = npool;
     bool overflow = false;
     if (npool > P.K) {
-        // rank by v descending (ties: slot index)
-        unsigned long long vk[S];
-#pragma unroll
-        for (int i = 0; i < S; ++i)
-            vk[i] = ((unsigned long long)(~orderable(v[i])) << 32) | (unsigned)(lane + 32 * i);
-        int rk[S];
-        warp_rank(vk, rk);
         float vK = -__int_as_float(0x7f800000), ncmax = 0.f, vabs = 0.f;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            if (off[i] >= 0 && rk[i] == P.K - 1) vK = v[i];
-            if (off[i] >= 0 && rk[i] < P.K) {
+            const int k = lane + 32 * i;
+            if (k == P.K - 1) vK = v[i];
+            if (k < P.K) {
                 ncmax = fmaxf(ncmax, nc[i]);
                 vabs = fmaxf(vabs, fabsf(v[i]));
             }
@@ -276,30 +288,28 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         for (int i = 0; i < S; ++i) {
             key[i] = kNone;
             if (member[i]) {
-                const float d32 = direct_f32(P, ref, off[i] / P.W, off[i] % P.W);
+                const float d32 = direct_f32(X, P.p, P.C, ref, off[i] / J.W, off[i] % J.W);
                 key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)off[i];
                 // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
                 const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
                 if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + 2.0f * P.round_rel * fabsf(v[i]) +
-                                          gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
+                                          P.gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
                     ++viol;
             }
         }
         for (int o = 16; o > 0; o >>= 1) viol += __shfl_xor_sync(0xffffffffu, viol, o);
         if (lane == 0 && viol) atomicAdd(P.counters + 2, (unsigned long long)viol);
-        select_and_write<S>(P, ref, key, nb, lane, r, gamma);
+        select_and_write<S>(P, J, X, ref, key, nb, lane, r);
         return;
     }
 
     // ---- overflow: exact top-(K+1) over the whole window, FP32 direct distances
     if (lane == 0) atomicAdd(P.counters + 0, 1ull);
-    unsigned long long* list = list_s[warp];
     const int nl = P.K + 1;
     for (int e = lane; e < kFbSlots * 32; e += 32) list[e] = kNone;
     __syncwarp();
-    const int Hc = P.H - P.p + 1;
-    const int y0 = max(0, yr - P.h), y1 = min(Hc - 1, yr + P.h);
-    const int x0 = max(0, xr - P.h), x1 = min(P.Wc - 1, xr + P.h);
+    const int y0 = max(0, yr - P.h), y1 = min(J.Hc - 1, yr + P.h);
+    const int x0 = max(0, xr - P.h), x1 = min(J.Wc - 1, xr + P.h);
     const int nxw = x1 - x0 + 1;
     const int total = (y1 - y0 + 1) * nxw;
     for (int base = 0; base < total; base += 32) {
@@ -307,8 +317,8 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         unsigned long long k = kNone;
         if (i < total) {
             const int yc = y0 + i / nxw, xc = x0 + i % nxw;
-            const float d = direct_f32(P, ref, yc, xc);
-            k = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * P.W + xc);
+            const float d = direct_f32(X, P.p, P.C, ref, yc, xc);
+            k = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * J.W + xc);
         }
         unsigned pass = __ballot_sync(0xffffffffu, k < list[nl - 1]);
         while (pass) {
@@ -341,31 +351,167 @@ __global__ void __launch_bounds__(kWarps * 32) rerank_kernel(const __grid_consta
         cnt += key2[t] != kNone ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    select_and_write<kFbSlots>(P, ref, key2, cnt, lane, r, gamma);
+    select_and_write<kFbSlots>(P, J, X, ref, key2, cnt, lane, r);
+}
+
+// Tile t of the launch: its job (binary search over the jobs' first tiles).
+__device__ __forceinline__ int tile_job(const RerankParams& P, int t) {
+    int lo = 0, hi = P.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ unsigned long long list_s[kTileWarps][kFbSlots * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x;
+    const RerankJob& J = P.jobs[tile_job(P, t)];
+    const int lt = t - J.tile_begin;
+    const int ry0 = (lt / J.tiles_x) * P.TRY, rx0 = (lt % J.tiles_x) * P.TRX;
+    const int ry1 = min(ry0 + P.TRY, J.n_ry) - 1, rx1 = min(rx0 + P.TRX, J.n_rx) - 1;
+    // region: every pixel of every window patch of the tile's references
+    const int iy0 = max(0, ry0 * P.s - P.h), iy1 = min(J.H - 1, ry1 * P.s + P.h + P.p - 1);
+    const int ix0 = max(0, rx0 * P.s - P.h), ix1 = min(J.W - 1, rx1 * P.s + P.h + P.p - 1);
+    const int ny1 = min(J.Hc - 1, ry1 * P.s + P.h), nx1 = min(J.Wc - 1, rx1 * P.s + P.h);
+    const int ipitch = (ix1 - ix0 + 1) * P.C, npitch = nx1 - ix0 + 1;
+    float* simg = sm;
+    float* snrm = sm + P.img_cap;
+    const int irows = iy1 - iy0 + 1, nrows = ny1 - iy0 + 1;
+    for (int i = threadIdx.x; i < irows * ipitch; i += blockDim.x) {
+        const int y = i / ipitch, e = i % ipitch;
+        simg[i] = __ldg(J.img + ((size_t)(iy0 + y) * J.W + ix0) * P.C + e);
+    }
+    for (int i = threadIdx.x; i < nrows * npitch; i += blockDim.x) {
+        const int y = i / npitch, x = i % npitch;
+        snrm[i] = __ldg(J.nrm + (size_t)(iy0 + y) * J.Wc + ix0 + x);
+    }
+    __syncthreads();
+    const Pix X{simg, iy0, ix0, ipitch, P.C};
+    const Pix N{snrm, iy0, ix0, npitch, 1};
+    const int ncols = rx1 - rx0 + 1;
+    const int nref = (ry1 - ry0 + 1) * ncols;
+    for (int i = warp; i < nref; i += kTileWarps)
+        rerank_ref<S>(P, J, X, N, ry0 + i / ncols, rx0 + i % ncols, lane, list_s[warp]);
+}
+
+// The same steps on global memory: one image, one reference per warp.
+template <int S>
+__global__ void __launch_bounds__(128) rerank_global_kernel(const __grid_constant__ RerankParams P) {
+    __shared__ unsigned long long list_s[4][kFbSlots * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RerankJob& J = P.jobs[0];
+    const size_t r = (size_t)blockIdx.x * 4 + warp;
+    if (r >= (size_t)J.n_ry * J.n_rx) return;
+    const Pix X{J.img, 0, 0, J.W * P.C, P.C};
+    const Pix N{J.nrm, 0, 0, J.Wc, 1};
+    rerank_ref<S>(P, J, X, N, (int)(r / J.n_rx), (int)(r % J.n_rx), lane, list_s[warp]);
+}
+
+// Tile shape and shared memory for a class; false: no region fits.
+bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
+    static const int kShapes[5][2] = {{8, 8}, {4, 8}, {4, 4}, {2, 2}, {1, 1}};
+    for (const auto& sh : kShapes) {
+        const int rows = (sh[0] - 1) * g.s + 2 * g.h + g.p;
+        const int cols = (sh[1] - 1) * g.s + 2 * g.h + g.p;
+        img_cap = (rows * cols * g.C + 3) / 4 * 4;
+        smem = (img_cap + rows * cols) * 4;
+        if (smem <= kTileSmemLimit) {
+            TRY = sh[0];
+            TRX = sh[1];
+            return true;
+        }
+    }
+    return false;
+}
+
+template <int S>
+cudaError_t launch_s(const RerankParams& P, bool tiled, int smem, int grid, cudaStream_t st) {
+    if (tiled) {
+        cudaFuncSetAttribute(rerank_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        rerank_tile_kernel<S><<<grid, kTileWarps * 32, smem, st>>>(P);
+    } else {
+        rerank_global_kernel<S><<<grid, 128, 0, st>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+RerankJob make_job(const Geom& g, const RerankArgs& a) {
+    RerankJob j{};
+    j.img = a.img; j.nrm = a.nrm; j.pool_idx = a.pool_idx; j.pool_score = a.pool_score;
+    j.out_idx = a.out_idx; j.out_dist = a.out_dist;
+    j.H = g.H; j.W = g.W; j.n_ry = g.n_ry; j.n_rx = g.n_rx; j.Hc = g.Hc; j.Wc = g.Wc;
+    return j;
 }
 
 }  // namespace
 
+bool rerank_same_class(const Geom& a, const Geom& b) {
+    return a.C == b.C && a.p == b.p && a.h == b.h && a.s == b.s && a.K == b.K && a.L == b.L &&
+           tc_score_bits(a) == tc_score_bits(b);
+}
+
+cudaError_t launch_rerank_batch(const Geom* gs, const RerankArgs* as, int n,
+                                unsigned long long* counters, cudaStream_t st, int* nlaunch) {
+    if (nlaunch) *nlaunch = 0;
+    int i = 0;
+    while (i < n) {
+        static thread_local RerankParams P;
+        P = RerankParams{};
+        const Geom& g = gs[i];
+        P.C = g.C; P.p = g.p; P.h = g.h; P.s = g.s; P.K = g.K; P.L = g.L;
+        const int tb = tc_score_bits(g);
+        P.round_rel = tb ? ldexpf(1.0f, tb - 23) : 0.0f;
+        P.gamma = (float)(g.p * g.p * g.C + 3) * 5.9604645e-08f;  // (n + 3) 2^-24
+        P.counters = counters;
+        const int S = (g.L + 31) / 32;
+        if (S < 1 || S > 5) return cudaErrorNotSupported;
+        int smem = 0;
+        const bool tiled = tile_shape(g, P.TRY, P.TRX, P.img_cap, smem);
+        int nj = 0, tiles = 0, grid;
+        if (tiled) {
+            while (i < n && nj < kMaxRerankJobs && rerank_same_class(gs[i], g)) {
+                RerankJob& j = P.jobs[nj];
+                j = make_job(gs[i], as[i]);
+                j.tiles_x = (gs[i].n_rx + P.TRX - 1) / P.TRX;
+                j.tile_begin = tiles;
+                tiles += j.tiles_x * ((gs[i].n_ry + P.TRY - 1) / P.TRY);
+                ++nj;
+                ++i;
+            }
+            grid = tiles;
+        } else {
+            P.jobs[0] = make_job(gs[i], as[i]);
+            nj = 1;
+            ++i;
+            grid = (g.nR + 3) / 4;
+        }
+        P.njobs = nj;
+        P.total_tiles = tiles;
+        cudaError_t e;
+        switch (S) {
+            case 1: e = launch_s<1>(P, tiled, smem, grid, st); break;
+            case 2: e = launch_s<2>(P, tiled, smem, grid, st); break;
+            case 3: e = launch_s<3>(P, tiled, smem, grid, st); break;
+            case 4: e = launch_s<4>(P, tiled, smem, grid, st); break;
+            default: e = launch_s<5>(P, tiled, smem, grid, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        if (nlaunch) ++*nlaunch;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_rerank(const Geom& g, const float* img, const float* nrm,
                           const int32_t* pool_idx, const float* pool_score, int32_t* out_idx,
                           float* out_dist, unsigned long long* counters, cudaStream_t st) {
-    RerankParams P{};
-    P.img = img; P.nrm = nrm; P.pool_idx = pool_idx; P.pool_score = pool_score;
-    P.out_idx = out_idx; P.out_dist = out_dist; P.counters = counters;
-    P.H = g.H; P.W = g.W; P.C = g.C; P.p = g.p; P.h = g.h; P.s = g.s; P.K = g.K; P.L = g.L;
-    P.n_ry = g.n_ry; P.n_rx = g.n_rx; P.Wc = g.Wc; P.nR = g.nR;
-    const int tb = tc_score_bits(g);
-    P.round_rel = tb ? ldexpf(1.0f, tb - 23) : 0.0f;
-    const int blocks = (g.nR + kWarps - 1) / kWarps;
-    switch ((g.L + 31) / 32) {
-        case 1: rerank_kernel<1><<<blocks, kWarps * 32, 0, st>>>(P); break;
-        case 2: rerank_kernel<2><<<blocks, kWarps * 32, 0, st>>>(P); break;
-        case 3: rerank_kernel<3><<<blocks, kWarps * 32, 0, st>>>(P); break;
-        case 4: rerank_kernel<4><<<blocks, kWarps * 32, 0, st>>>(P); break;
-        case 5: rerank_kernel<5><<<blocks, kWarps * 32, 0, st>>>(P); break;
-        default: return cudaErrorNotSupported;
-    }
-    return cudaGetLastError();
+    const RerankArgs a{img, nrm, pool_idx, pool_score, out_idx, out_dist};
+    return launch_rerank_batch(&g, &a, 1, counters, st);
 }
 
 }  // namespace bm

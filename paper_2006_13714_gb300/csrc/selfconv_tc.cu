@@ -950,11 +950,11 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             // ---- write results
             if (lane_ok && !*abort_flag) {
                 const size_t ref = (size_t)ry * J.n_rx + rx;
-                if constexpr (LC == 0 && !kF32) heap.sort();
+                if constexpr (LC == 0) heap.sort();  // outputs and pools best first
                 const int nout = kF32 ? G.HL : G.K;
                 auto emit = [&](int i, unsigned long long key) {
                     if (kF32) {
-                        // pool: any order; the re-rank kernel ranks it
+                        // pool: best first (the list order)
                         J.pool_idx[ref * G.HL + i] =
                             key == kEmpty ? -1 : (int32_t)(unsigned)(key & 0xffffffffu);
                         J.pool_score[ref * G.HL + i] =
