@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--images", type=int, default=160, help="512^2 images per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving latency stream")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--minimal", action="store_true",
                     help="timed loop only (no baselines, latency or e2e); for profiler runs")
@@ -215,6 +216,79 @@ def run_reference(args, world, rank, dist):
 
 # ---------------------------------------------------------------- our arm
 
+def serve_latency(ctx, pkg, synth, dev, n=160, seed=SEED_BASE + 55):
+    """Serving: a seeded Poisson stream of mixed requests (shapes of the
+    serving workload: uint8/float32, C in {1, 4}, patch 7/8, window 39/61,
+    K 16/32/70; sides drawn in [128, 768] to bound the run) submitted to the
+    context's queue at their arrival times; per-request latency = completion
+    seen by polling - arrival.  The rate is 0.7 x the serial throughput of a
+    calibration pass (requests matched one after another)."""
+    import torch
+    draws = synth.serve_requests(n, seed, 1.0)
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for d in draws:
+        H = 128 + int(d["H"] - 128) * (768 - 128) // (2048 - 128)
+        W = 128 + int(d["W"] - 128) * (768 - 128) // (2048 - 128)
+        dt = np.uint8 if d["dtype"] == "u8" else np.float32
+        if d["C"] == 1:
+            img = synth.gray(H, W, 20.0, d["seed"], dt)
+        else:
+            img = np.ascontiguousarray(np.stack(
+                [synth.gray(H, W, 20.0, d["seed"] * 4 + c, dt) for c in range(4)], axis=-1))
+        t = torch.from_numpy(img).to(dev)
+        idx, dist_t = ctx.outputs(t, d["patch"], d["stride"], d["K"])
+        req = pkg.Context.request(t, d["patch"], d["window"], d["stride"], d["K"], idx, dist_t)
+        jobs.append((t, idx, dist_t, req))
+    torch.cuda.synchronize(dev)
+
+    def wait(ticket):
+        t_end = time.perf_counter() + 120.0
+        while True:
+            if time.perf_counter() > t_end:
+                raise RuntimeError("serving request did not finish in 120 s")
+            done, st = ctx.poll(ticket)
+            if done:
+                if st != 0:
+                    raise pkg.BMError(st, "serving request failed")
+                return
+
+    # calibration: serial throughput over a prefix of the stream
+    t0 = time.perf_counter()
+    ncal = 24
+    for j in jobs[:ncal]:
+        wait(ctx.submit(j[3]))
+    serial_rps = ncal / (time.perf_counter() - t0)
+    rate = 0.7 * serial_rps
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    lat = [None] * n
+    tickets = {}
+    start = time.perf_counter()
+    i = 0
+    while i < n or tickets:
+        now = time.perf_counter() - start
+        if now > arrivals[-1] + 120.0:
+            raise RuntimeError("serving stream did not finish in 120 s after the last arrival")
+        while i < n and arrivals[i] <= now:
+            tickets[ctx.submit(jobs[i][3])] = i
+            i += 1
+        for tk in list(tickets):
+            done, st = ctx.poll(tk)
+            if done:
+                if st != 0:
+                    raise pkg.BMError(st, "serving request failed")
+                k = tickets.pop(tk)
+                lat[k] = (time.perf_counter() - start) - arrivals[k]
+        time.sleep(0.0001)
+    wall = time.perf_counter() - start
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": n, "rate_req_per_s": rate, "serial_req_per_s": serial_rps,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "throughput_req_per_s": n / wall,
+            "workload": "Poisson arrivals; u8/f32, C 1/4, patch 7/8, window 39/61, K 16/32/70, "
+                        "sides 128-768 (seeded)"}
+
+
 def run_ours(args, world, rank, local, dist):
     import torch
     import paper_2006_13714_gb300 as pkg
@@ -242,7 +316,8 @@ def run_ours(args, world, rank, local, dist):
         imgs.append(t)
         outs.append((idx, dist_t))
         reqs.append(pkg.Context.request(t, p, win, s, K, idx, dist_t))
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own: repeated batches replay one captured CUDA graph
+    stream = torch.cuda.Stream(dev)
 
     def step():
         ctx.match_batch(reqs, stream=stream)
@@ -254,8 +329,6 @@ def run_ours(args, world, rank, local, dist):
 
     clocks = ClockSampler(local)
     clocks.start()
-    ctx.timing(reset=True)
-    ctx.set_timing(True)
     barrier(dist)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -265,11 +338,18 @@ def run_ours(args, world, rank, local, dist):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(dist)
-    ctx.set_timing(False)
     elapsed_ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    tm = ctx.timing(reset=True)
     elapsed_ms = max_over_ranks(dist, elapsed_ms, dev)
+    # per-kernel device times: the same steps again with the library's stage
+    # events (CUDA events on the launch stream around every kernel launch)
+    ctx.timing(reset=True)
+    ctx.set_timing(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(False)
+    tm = ctx.timing(reset=True)
     total_refs = nR * B * args.steps * world
     value = total_refs / (elapsed_ms / 1e3)
     st1 = ctx.stats()
@@ -284,13 +364,7 @@ def run_ours(args, world, rank, local, dist):
         ctx.close()
         return 0
 
-    # the same batch without stage events (host launch overhead check)
-    e0.record(stream)
-    for _ in range(max(2, args.steps // 4)):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    untimed_ms = e0.elapsed_time(e1) / max(2, args.steps // 4)
+    staged_ms = sum(v["ms"] for v in tm.values()) / args.steps
 
     # roofline of the dominant kernel (tensor-core cross term + top-K)
     peaks = {}
@@ -349,6 +423,8 @@ def run_ours(args, world, rank, local, dist):
     e2e_s = max_over_ranks(dist, e2e_s, dev)
     e2e_value = nR * n_e2e * e2e_steps * world / e2e_s
 
+    serve = serve_latency(ctx, pkg, synth, dev) if not args.no_serve else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, n_img, el = cpu_oracle_rate(args.cpu_seconds, SEED_BASE + 100)
@@ -378,7 +454,8 @@ def run_ours(args, world, rank, local, dist):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "stage_ms_share": stage_share,
-        "ms_per_step_without_stage_events": untimed_ms,
+        "kernel_ms_per_step_with_stage_events": staged_ms,
+        "serve": serve,
         "direct_fp32_gpu": {"ms_per_image": direct_ms_img, "ms_per_image_selfconv": tc_ms_img,
                             "speedup": direct_ms_img / tc_ms_img},
         "single_image_latency_ms": {"min": min(lat), "median": statistics.median(lat)},

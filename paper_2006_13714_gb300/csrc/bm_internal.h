@@ -104,7 +104,10 @@ cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
 // Several jobs in persistent launches (consecutive jobs of one class share a
 // launch, up to 64 jobs each); *nlaunch (nullable) = kernel launches made.
 cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st,
-                            int* nlaunch = nullptr);
+                            int* nlaunch = nullptr, const int* choices = nullptr);
+// Tile configurations the tensor-core kernel can run a job shape with
+// (choices[i] in launch_tc_batch: 0 .. n-1; -1 = the built-in heuristic).
+int tc_num_choices(const Geom& g);
 bool tc_supported(const Geom& g);
 // float32 pool scores of the tensor-core pass are rounded up by less than
 // 2^bits ulp (0: exact float32 scores).

@@ -1008,7 +1008,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 // Preference: two tiles in flight (when the list lives in registers), then
 // the mapping with the least MMA work, then the largest append buffer and
 // the deepest stage ring that fit the shared memory.
-bool make_tc_geom(const Geom& g, TcGeom& t) {
+bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nullptr) {
     t = TcGeom{};
     t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
     t.pw = g.pw; t.p_eff = g.p_eff; t.nkc = g.p_eff * g.pw;
@@ -1033,6 +1033,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
         bool found = false;
         long long best = 0;
         TcGeom bestc{};
+        int ncand = 0;
         for (const auto& mp : kMaps)
             for (int kbuf = 32; kbuf >= 16; kbuf -= 16)
                 for (int nst = kMaxSt; nst >= 2; --nst) {
@@ -1072,6 +1073,12 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
                     c.off_bar = off; off += ns * kBarsPerSlot * 8 + 16;
                     c.smem_total = (off + 1023) / 1024 * 1024;
                     if (c.smem_total > kSmemLimit) continue;
+                    // an explicit choice (autotuner) is the choice-th fitting candidate
+                    if (ncand++ == choice) {
+                        t = c;
+                        if (nchoices) *nchoices = -1;  // counting stops at the pick
+                        return true;
+                    }
                     // least MMA work (union columns x strip rows); among equals the
                     // first fit: the larger append buffer, then deeper stages
                     const long long work = (long long)nx_max * c.Rb;
@@ -1082,6 +1089,8 @@ bool make_tc_geom(const Geom& g, TcGeom& t) {
                     }
                 }
         if (found) {
+            if (nchoices) *nchoices = ncand;
+            if (choice >= ncand) return false;  // no such candidate
             t = bestc;
             return true;
         }
@@ -1184,6 +1193,12 @@ bool tc_supported(const Geom& g) {
     return make_tc_geom(g, t);
 }
 
+int tc_num_choices(const Geom& g) {
+    TcGeom t{};
+    int n = 0;
+    return make_tc_geom(g, t, -1, &n) ? n : 0;
+}
+
 int tc_score_bits(const Geom& g) {
     TcGeom t{};
     return make_tc_geom(g, t) ? t.tbits : 0;
@@ -1200,16 +1215,18 @@ cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_t st,
-                            int* nlaunch) {
+                            int* nlaunch, const int* choices) {
     int i = 0;
     if (nlaunch) *nlaunch = 0;
     while (i < n) {
         static thread_local TcParams P;
         P = TcParams{};
-        if (!make_tc_geom(gs[i], P.g)) return cudaErrorNotSupported;
+        const int choice = choices ? choices[i] : -1;
+        if (!make_tc_geom(gs[i], P.g, choice)) return cudaErrorNotSupported;
         P.status = as[i].status;
         int tiles = 0, nj = 0;
-        while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj])) {
+        while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj]) &&
+               (choices ? choices[i] : -1) == choice) {
             if (!make_job(P.jobs[nj], gs[i], P.g, as[i], tiles)) return cudaErrorInvalidValue;
             tiles += P.jobs[nj].tiles_x * ((gs[i].n_ry + P.g.ty - 1) / P.g.ty);
             ++nj;
