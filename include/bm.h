@@ -104,7 +104,10 @@ typedef struct {
 /*
  * Create a context on CUDA device `device`.  mem_budget_bytes bounds the
  * library's own device workspace (0 = 40 GiB).  tune_cache (nullable) is
- * a file path where tuned tile choices are read from and written to.
+ * a file path where tuned tile choices are read from and written to: with
+ * it, the first job of each class (dtype, channels, patch, window, stride,
+ * K) times every tile configuration of the tensor-core kernel on its own
+ * data and keeps the fastest whose output equals the default's.
  * Returns BM_OK and *out, or an error (then *out is NULL).
  */
 int bm_create(bm_ctx** out, int device, size_t mem_budget_bytes, const char* tune_cache);
@@ -151,8 +154,10 @@ int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dt
 /*
  * Match n independent jobs (any mix of sizes, channel counts, dtypes and
  * parameters) with one persistent launch per kernel stage, asynchronous on
- * `stream`.  Same per-job conventions as bm_match.  Replays of an
- * identical job list reuse a captured CUDA graph.
+ * `stream`.  Same per-job conventions as bm_match.  On a stream other than
+ * the legacy default stream, and with stage timing off, a call with the same
+ * job list (same descriptors) as the previous call on that stream replays a
+ * captured CUDA graph of the whole batch.
  */
 int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream);
 
@@ -221,7 +226,7 @@ int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset);
  * whose working set (bm_static_scratch_bytes) exceeds the array returns
  * BM_ERR_TOO_LARGE with nothing launched; bm_last_error(NULL) says how many
  * bytes it needed.  For reference, a 512 x 512 float32 image with patch 8,
- * stride 3, window 39, K 16 needs about 9.5 MB.
+ * stride 3, window 39, K 16 needs about 13.5 MB.
  *
  * Set-up: the first call on a device (the current device) looks up the
  * array's address there with cudaGetSymbolAddress.  Make that first call
