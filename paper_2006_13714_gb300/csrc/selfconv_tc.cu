@@ -257,18 +257,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         : "memory");
 }
 
-// 16 bytes starting SH bf16 elements into the 32 bytes {a, b}.
-template <int SH>
-__device__ __forceinline__ uint4 shift_words(const uint4& a, const uint4& b) {
-    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    constexpr int j = SH >> 1;
-    if constexpr ((SH & 1) != 0)
-        return make_uint4(__funnelshift_r(w[j], w[j + 1], 16), __funnelshift_r(w[j + 1], w[j + 2], 16),
-                          __funnelshift_r(w[j + 2], w[j + 3], 16), __funnelshift_r(w[j + 3], w[j + 4], 16));
-    else
-        return make_uint4(w[j], w[j + 1], w[j + 2], w[j + 3]);
-}
-
 // 16 bytes of a staged row starting at element e (any alignment; per-lane e).
 __device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
     const uint4* s = reinterpret_cast<const uint4*>(row + (e >> 3) * 16);
@@ -287,41 +275,57 @@ __device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
                       __funnelshift_r(v[2], v[3], f), __funnelshift_r(v[3], v[4], f));
 }
 
-// Strip rows [lane, Rb) step 32: dst row = 16 bytes of staged row `row`
-// starting SH elements past src (the shift is the same for the whole strip).
-template <int SH>
-__device__ __forceinline__ void copy_strip(const uint8_t* src, int pitch, uint8_t* dst, int Rb,
-                                           int lane) {
-    // Rb is a multiple of 16: rows lane, lane + 32, ... two loads in flight
+// Words J .. J+3 of the 32 bytes {a, b}, each shifted right by f bits
+// (0 or 16): 16 bytes starting 2J + f/16 bf16 elements in.
+template <int J>
+__device__ __forceinline__ uint4 shift_pair(const uint4& a, const uint4& b, uint32_t f) {
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    return make_uint4(__funnelshift_r(w[J], w[J + 1], f), __funnelshift_r(w[J + 1], w[J + 2], f),
+                      __funnelshift_r(w[J + 2], w[J + 3], f), __funnelshift_r(w[J + 3], w[J + 4], f));
+}
+
+// Column strips of NP planes at once: strip row `row` (rows lane, lane + 32,
+// ... < Rb) of plane pl = the 16 bytes of staged row `row` starting 2J + f/16
+// elements past src[pl] (the same shift for every row).  Two rows per lane
+// and every plane in flight per step.
+template <int J, int NP>
+__device__ __forceinline__ void copy_strips_j(const uint8_t* const (&src)[2], uint8_t* const (&dst)[2],
+                                              int pitch, int Rb, int lane, uint32_t f) {
     for (int r0 = 0; r0 < Rb; r0 += 64) {
-        const int row0 = r0 + lane, row1 = row0 + 32;
-        uint4 a0 = make_uint4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
-        if (row0 < Rb) {
-            const uint4* s = reinterpret_cast<const uint4*>(src + row0 * pitch);
-            a0 = s[0];
-            b0 = SH ? s[1] : a0;
-        }
-        if (row1 < Rb) {
-            const uint4* s = reinterpret_cast<const uint4*>(src + row1 * pitch);
-            a1 = s[0];
-            b1 = SH ? s[1] : a1;
-        }
-        if (row0 < Rb) *reinterpret_cast<uint4*>(dst + row0 * 16) = shift_words<SH>(a0, b0);
-        if (row1 < Rb) *reinterpret_cast<uint4*>(dst + row1 * 16) = shift_words<SH>(a1, b1);
+        uint4 a[NP][2], b[NP][2];
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int row = r0 + lane + 32 * t;
+                if (row < Rb) {
+                    const uint4* sp = reinterpret_cast<const uint4*>(src[pl] + row * pitch);
+                    a[pl][t] = sp[0];
+                    b[pl][t] = sp[1];
+                }
+            }
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int row = r0 + lane + 32 * t;
+                if (row < Rb)
+                    *reinterpret_cast<uint4*>(dst[pl] + row * 16) = shift_pair<J>(a[pl][t], b[pl][t], f);
+            }
     }
 }
 
-__device__ __forceinline__ void copy_strip_any(int sh, const uint8_t* src, int pitch, uint8_t* dst,
-                                               int Rb, int lane) {
-    switch (sh) {
-        case 0: copy_strip<0>(src, pitch, dst, Rb, lane); break;
-        case 1: copy_strip<1>(src, pitch, dst, Rb, lane); break;
-        case 2: copy_strip<2>(src, pitch, dst, Rb, lane); break;
-        case 3: copy_strip<3>(src, pitch, dst, Rb, lane); break;
-        case 4: copy_strip<4>(src, pitch, dst, Rb, lane); break;
-        case 5: copy_strip<5>(src, pitch, dst, Rb, lane); break;
-        case 6: copy_strip<6>(src, pitch, dst, Rb, lane); break;
-        default: copy_strip<7>(src, pitch, dst, Rb, lane); break;
+// Element shift sh (0..7) of a strip: word offset sh / 2 (compile-time
+// case), half-word funnel shift (sh & 1) * 16 bits (run time).
+template <int NP>
+__device__ __forceinline__ void copy_strips(int sh, const uint8_t* const (&src)[2],
+                                            uint8_t* const (&dst)[2], int pitch, int Rb, int lane) {
+    const uint32_t f = (uint32_t)(sh & 1) * 16u;
+    switch (sh >> 1) {
+        case 0: copy_strips_j<0, NP>(src, dst, pitch, Rb, lane, f); break;
+        case 1: copy_strips_j<1, NP>(src, dst, pitch, Rb, lane, f); break;
+        case 2: copy_strips_j<2, NP>(src, dst, pitch, Rb, lane, f); break;
+        default: copy_strips_j<3, NP>(src, dst, pitch, Rb, lane, f); break;
     }
 }
 
@@ -769,15 +773,15 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
                 const int kc_here = min(G.kcols, T.NX - jc0);
                 // strips (the stage was freed before its norms were issued)
-                for (int pl = 0; pl < nplanes; ++pl)
-                    for (int q = 0; q < G.pw; ++q)
-                        for (int jl = 0; jl < kc_here; ++jl) {
-                            const int ecol = delta + (jc0 + jl) * G.Cp + 8 * q;
-                            copy_strip_any(ecol & 7, sbase + pl * G.base_bytes + (ecol >> 3) * 16,
-                                           G.base_pitch,
-                                           sb + pl * G.plane_stage + q * G.qpitch + jl * G.Rb * 16,
-                                           G.Rb, lane);
-                        }
+                for (int q = 0; q < G.pw; ++q)
+                    for (int jl = 0; jl < kc_here; ++jl) {
+                        const int ecol = delta + (jc0 + jl) * G.Cp + 8 * q;
+                        const uint8_t* const src[2] = {sbase + (ecol >> 3) * 16,
+                                                       sbase + G.base_bytes + (ecol >> 3) * 16};
+                        uint8_t* const dst[2] = {sb + q * G.qpitch + jl * G.Rb * 16,
+                                                 sb + G.plane_stage + q * G.qpitch + jl * G.Rb * 16};
+                        copy_strips<nplanes>(ecol & 7, src, dst, G.base_pitch, G.Rb, lane);
+                    }
                 // norms of the next chunk of this tile
                 if (c + 1 < T.nchunks && !__all_sync(0xffffffffu, issue_norm(T, c + 1, cs + 1))) {
                     ok = false;
@@ -1064,7 +1068,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
                     c.off_base = off; off += (nplanes * c.base_bytes + 1023) / 1024 * 1024;
                     c.off_a = off; off += nplanes * c.a_bytes;
                     c.off_stage = off; off += nst * c.stage_bytes;
-                    c.off_buf = off; off += 128 * kbuf * 8;
+                    c.off_buf = off; off += 128 * kbuf * (c.tbits ? 4 : 8);  // 32- or 64-bit keys
                     c.slot_bytes = (off + 1023) / 1024 * 1024;
                     off = 0;
                     c.off_slots = off; off += ns * c.slot_bytes;
