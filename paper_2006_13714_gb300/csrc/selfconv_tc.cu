@@ -44,12 +44,12 @@
 // columns arrive by bulk copy (cp.async.bulk), one contiguous column each.
 //
 // Slots.  A CTA keeps NS tiles in flight.  Slot k owns epilogue warps
-// 4k..4k+3 (warp 4k+i reads TMEM lanes 32i..32i+31), one control warp
-// (TMA issue, operand formation, single-thread MMA issue), its own shared-
-// memory regions and two TMEM accumulators, so the slots never wait on each
-// other; they share only the tensor core.  Every wait is bounded; on timeout
-// the CTA sets *status, waits for its copies and MMAs in flight, frees its
-// TMEM and returns.
+// 4k..4k+3 (warp 4k+i reads TMEM lanes 32i..32i+31), one producer warp (TMA
+// issue, operand formation), one MMA warp (single-thread MMA issue), its own
+// shared-memory regions and two TMEM accumulators, so the slots never wait
+// on each other; they share only the tensor core.  Every wait is bounded; on
+// timeout the CTA sets *status, waits for its copies and MMAs in flight,
+// frees its TMEM and returns.
 #include "bm_internal.h"
 
 #include <cuda.h>
@@ -66,8 +66,9 @@ constexpr int kSmemLimit = 227 * 1024;
 constexpr int kBatch = 8;  // keys merged into the register list at a time
 constexpr int kMaxSt = 3;  // stages per slot (upper bound)
 
-// Threads of a CTA with NS slots: 4 epilogue warps + 1 control warp per slot.
-__host__ __device__ constexpr int cta_threads(int ns) { return ns * 160; }
+// Threads of a CTA with NS slots: 4 epilogue warps, 1 producer warp and 1
+// MMA warp per slot.
+__host__ __device__ constexpr int cta_threads(int ns) { return ns * 192; }
 
 // Class-wide geometry of one launch (every job shares patch, window, stride,
 // K, channel padding and dtype; image sizes are per job).
@@ -235,6 +236,10 @@ __device__ __forceinline__ float from_orderable(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
@@ -592,8 +597,10 @@ enum : int {
     kBarTFull = 3,                // [2] accumulator ready for the epilogue
     kBarTEmpty = 5,               // [2] accumulator drained by the epilogue (128 arrivals)
     kBarSEmpty = 7,               // [kMaxSt] stage free (MMAs done reading it)
-    kBarNFull = 7 + kMaxSt,       // [kMaxSt] stage's split norms landed (bulk copy, tx count)
-    kBarsPerSlot = 7 + 2 * kMaxSt
+    kBarFull = 7 + kMaxSt,        // [kMaxSt] stage filled: strips formed (producer
+                                  //   arrival) and split norms landed (bulk copy, tx count)
+    kBarAFull = 7 + 2 * kMaxSt,   // A of the slot's current tile formed (producer)
+    kBarsPerSlot = 8 + 2 * kMaxSt
 };
 
 // Bounded wait that ignores the abort flag (draining copies in flight).
@@ -636,13 +643,15 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             }
             for (int i = 0; i < kMaxSt; ++i) {
                 mbar_init(BAR(k, kBarSEmpty + i), 1);
-                mbar_init(BAR(k, kBarNFull + i), 1);
+                mbar_init(BAR(k, kBarFull + i), 1);
             }
+            mbar_init(BAR(k, kBarAFull), 1);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kEpiWarps) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    constexpr int kMmaWarp0 = kEpiWarps + NS;  // MMA warp of slot k: kMmaWarp0 + k
+    if (warp == kMmaWarp0) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
     // A_norm (shared by all tiles): [group][2 kchunks][8 x 16 B], the
     // coefficients of the norm pieces
     for (int t = threadIdx.x; t < 128 * 2; t += kThreads) {
@@ -668,42 +677,16 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp >= kEpiWarps) {
-        // ------------------------------------------------------------ control warp of slot k
+    if (warp >= kEpiWarps && warp < kMmaWarp0) {
+        // ------------------------------------------------------------ producer warp of slot k
         const int k = warp - kEpiWarps;
         uint8_t* slot = smem + G.off_slots + k * G.slot_bytes;
         uint8_t* sbase = slot + G.off_base;
         uint8_t* sa = slot + G.off_a;
-        const uint32_t an = smem_u32(smem + G.off_an);
-        const uint32_t sbo_a = G.nkc * 128;
-        const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
         const uint32_t box_bytes = (uint32_t)G.nc_box * 16u * (uint32_t)G.Rb;
-        // copies in flight (for the drain on abort): base phase, norm phase per stage
-        int base_pending = -1;
-        int norm_pending[kMaxSt];
-        for (int i = 0; i < kMaxSt; ++i) norm_pending[i] = -1;
-        int cs = 0;  // slot-local chunk counter: stage ring and accumulator phases
+        int base_pending = -1;  // staged-tile copy in flight (drained on abort)
+        int cs = 0;             // slot-local chunk counter: stage ring
         bool ok = true;
-        // Split norms of chunk c of tile T into stage (cs' % nst): one bulk
-        // copy per candidate column (rows Y0 .. min(Y0 + Rb, Hc) - 1).
-        auto issue_norm = [&](const TileInfo& T, int c, int csn) -> bool {
-            const int st = csn % G.nst, use = csn / G.nst;
-            if (use > 0 && !mbar_wait(BAR(k, kBarSEmpty + st), (use - 1) & 1, abort_flag, 1)) return false;
-            const TcJob& J = *T.job;
-            const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
-            const int kc_here = min(G.kcols, T.NX - jc0);
-            const int rows = min(G.Rb, J.Hc - T.Y0);
-            if (lane == 0) {
-                uint8_t* nsb = slot + G.off_stage + st * G.stage_bytes + nplanes * G.plane_stage;
-                mbar_arrive_expect_tx(BAR(k, kBarNFull + st), (uint32_t)(kc_here * rows * 16));
-                for (int jl = 0; jl < kc_here; ++jl)
-                    bulk_load(smem_u32(nsb + jl * G.Rb * 16),
-                              J.nsp + ((size_t)(T.X0 + jc0 + jl) * J.Hc + T.Y0) * 8,
-                              (uint32_t)(rows * 16), BAR(k, kBarNFull + st));
-            }
-            norm_pending[st] = use & 1;
-            return true;
-        };
         for (int turn = 0; ok && !*abort_flag; ++turn) {
             const int tile = slot_tile(cta, turn, k, NS, grid);
             if (tile >= P.total_tiles) break;
@@ -720,14 +703,12 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                                 BAR(k, kBarBase));
             }
             base_pending = turn & 1;
-            // (2) norms of the first chunk
-            ok = __all_sync(0xffffffffu, issue_norm(T, 0, cs));
-            // (3) A region free (previous tile's MMAs done) and the tile landed
-            if (ok && turn > 0) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarAEmpty), (turn - 1) & 1, abort_flag, 5));
+            // (2) A region free (previous tile's MMAs done) and the tile landed
+            if (turn > 0) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarAEmpty), (turn - 1) & 1, abort_flag, 5));
             if (ok) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6));
             if (!ok) break;
             base_pending = -1;
-            // (4) A: reference patch rows cut from the staged tile; lane m
+            // (3) A: reference patch rows cut from the staged tile; lane m
             // takes references m, m + 32, ... (lane -> reference mapping of
             // the epilogue), kc = patch row u, 16-byte chunk q
             for (int m = lane; m < 128; m += 32) {
@@ -766,13 +747,29 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     }
                 }
             }
-            // (5) chunks of candidate columns
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(BAR(k, kBarAFull));
+            // (4) chunks: stage free -> split norms by bulk copy -> strips
+            // formed in place -> arrival on the stage's barrier
+            const int rows = min(G.Rb, J.Hc - T.Y0);
             for (int c = 0; c < T.nchunks; ++c, ++cs) {
                 const int stage = cs % G.nst, use = cs / G.nst;
+                if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(BAR(k, kBarSEmpty + stage), (use - 1) & 1, abort_flag, 1))) {
+                    ok = false;
+                    break;
+                }
                 uint8_t* sb = slot + G.off_stage + stage * G.stage_bytes;
                 const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
                 const int kc_here = min(G.kcols, T.NX - jc0);
-                // strips (the stage was freed before its norms were issued)
+                if (lane == 0) {
+                    uint8_t* nsb = sb + nplanes * G.plane_stage;
+                    mbar_expect_tx(BAR(k, kBarFull + stage), (uint32_t)(kc_here * rows * 16));
+                    for (int jl = 0; jl < kc_here; ++jl)
+                        bulk_load(smem_u32(nsb + jl * G.Rb * 16),
+                                  J.nsp + ((size_t)(T.X0 + jc0 + jl) * J.Hc + T.Y0) * 8,
+                                  (uint32_t)(rows * 16), BAR(k, kBarFull + stage));
+                }
                 for (int q = 0; q < G.pw; ++q)
                     for (int jl = 0; jl < kc_here; ++jl) {
                         const int ecol = delta + (jc0 + jl) * G.Cp + 8 * q;
@@ -782,59 +779,83 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                                                  sb + G.plane_stage + q * G.qpitch + jl * G.Rb * 16};
                         copy_strips<nplanes>(ecol & 7, src, dst, G.base_pitch, G.Rb, lane);
                     }
-                // norms of the next chunk of this tile
-                if (c + 1 < T.nchunks && !__all_sync(0xffffffffu, issue_norm(T, c + 1, cs + 1))) {
-                    ok = false;
-                    break;
-                }
                 fence_proxy_async();
                 __syncwarp();
-                int lok = 1;
-                if (lane == 0) {
-                    const int buf = cs & 1, ub = cs >> 1;
-                    if (ub > 0 && !mbar_wait(BAR(k, kBarTEmpty + buf), (ub - 1) & 1, abort_flag, 2)) lok = 0;
-                    if (lok && !mbar_wait(BAR(k, kBarNFull + stage), use & 1, abort_flag, 3)) lok = 0;
-                    if (lok) {
-                        tc_fence_after();
-                        const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
-                        const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
-                        const uint32_t sbu = smem_u32(sb);
-                        const uint32_t a0 = smem_u32(sa);
-                        const uint32_t a1 = a0 + G.a_bytes;
-                        uint32_t acc = 0;
-                        for (int t = 0; t < G.nkc / 2; ++t) {
-                            const int kc = 2 * t;
-                            const int u = kc / G.pw, qq = kc % G.pw;
-                            const uint32_t boff = qq * G.qpitch + u * 16;
-                            const uint64_t da0 = sdesc(a0 + kc * 128, 128, sbo_a);
-                            const uint64_t db0 = sdesc(sbu + boff, lbo_b, 128);
-                            mma_bf16(d, da0, db0, idesc, acc);
-                            acc = 1;
-                            if (kF32) {
-                                const uint64_t db1 = sdesc(sbu + G.plane_stage + boff, lbo_b, 128);
-                                const uint64_t da1 = sdesc(a1 + kc * 128, 128, sbo_a);
-                                mma_bf16(d, da0, db1, idesc, 1);
-                                mma_bf16(d, da1, db0, idesc, 1);
-                            }
-                        }
-                        mma_bf16(d, sdesc(an, 128, 256), sdesc(sbu + nplanes * G.plane_stage, 16, 128),
-                                 idesc, 1);
-                        mma_commit(BAR(k, kBarSEmpty + stage));
-                        mma_commit(BAR(k, kBarTFull + buf));
-                        if (c + 1 == T.nchunks) mma_commit(BAR(k, kBarAEmpty));
-                    }
-                }
-                ok = __shfl_sync(0xffffffffu, lok, 0) != 0;
-                if (!ok) break;
-                norm_pending[stage] = -1;
+                if (lane == 0) mbar_arrive(BAR(k, kBarFull + stage));
             }
         }
-        // drain: copies in flight, then every MMA issued by this slot, before
-        // the shared memory and TMEM are released
+        // drain the copies in flight before the shared memory is released:
+        // the staged tile, and the split norms of the last use of each stage
         if (lane == 0) {
             if (base_pending >= 0) mbar_drain(BAR(k, kBarBase), base_pending);
-            for (int i = 0; i < kMaxSt; ++i)
-                if (norm_pending[i] >= 0) mbar_drain(BAR(k, kBarNFull + i), norm_pending[i]);
+            for (int i = 0; i < G.nst && i < cs; ++i) {
+                const int csn = cs - 1 - i;
+                mbar_drain(BAR(k, kBarFull + csn % G.nst), (csn / G.nst) & 1);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kMmaWarp0) {
+        // ------------------------------------------------------------ MMA warp of slot k
+        const int k = warp - kMmaWarp0;
+        if (lane == 0) {
+            uint8_t* slot = smem + G.off_slots + k * G.slot_bytes;
+            const uint32_t an = smem_u32(smem + G.off_an);
+            const uint32_t sbo_a = G.nkc * 128;
+            const uint32_t lbo_b = G.pw == 1 ? 16u : (uint32_t)G.qpitch;
+            // descriptors: the start-address field (address >> 4) of a base
+            // descriptor plus the operand offset >> 4 (shared-memory addresses
+            // stay below 2^18, no carry out of the field)
+            const uint64_t da_hi = sdesc(smem_u32(slot + G.off_a), 128, sbo_a);
+            const uint64_t da_lo = da_hi + (uint64_t)(G.a_bytes >> 4);
+            const uint64_t dn_a = sdesc(an, 128, 256);
+            int cs = 0;
+            bool ok = true;
+            for (int turn = 0; ok; ++turn) {
+                const int tile = slot_tile(cta, turn, k, NS, grid);
+                if (tile >= P.total_tiles) break;
+                const TileInfo T = tile_info(P, tile);
+                if (!mbar_wait(BAR(k, kBarAFull), turn & 1, abort_flag, 7)) break;
+                for (int c = 0; c < T.nchunks; ++c, ++cs) {
+                    const int stage = cs % G.nst, use = cs / G.nst;
+                    const int buf = cs & 1, ub = cs >> 1;
+                    if (ub > 0 && !mbar_wait(BAR(k, kBarTEmpty + buf), (ub - 1) & 1, abort_flag, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait(BAR(k, kBarFull + stage), use & 1, abort_flag, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                    const int kc_here = min(G.kcols, T.NX - jc0);
+                    const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
+                    const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
+                    const uint32_t sbu = smem_u32(slot + G.off_stage + stage * G.stage_bytes);
+                    const uint64_t db_hi = sdesc(sbu, lbo_b, 128);
+                    const uint64_t db_lo = db_hi + (uint64_t)(G.plane_stage >> 4);
+                    uint32_t acc = 0;
+                    int u = 0, qq = 0;
+                    for (int kc = 0; kc < G.nkc; kc += 2) {
+                        const uint64_t oa = (uint64_t)(kc * 8);  // kc * 128 bytes
+                        const uint64_t ob = (uint64_t)((qq * G.qpitch + u * 16) >> 4);
+                        mma_bf16(d, da_hi + oa, db_hi + ob, idesc, acc);
+                        acc = 1;
+                        if (kF32) {
+                            mma_bf16(d, da_hi + oa, db_lo + ob, idesc, 1);
+                            mma_bf16(d, da_lo + oa, db_hi + ob, idesc, 1);
+                        }
+                        // next pair of 16-byte K chunks: (u, q) advances by two in row-major order
+                        qq += 2;
+                        while (qq >= G.pw) { qq -= G.pw; ++u; }
+                    }
+                    mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
+                    mma_commit(BAR(k, kBarSEmpty + stage));
+                    mma_commit(BAR(k, kBarTFull + buf));
+                    if (c + 1 == T.nchunks) mma_commit(BAR(k, kBarAEmpty));  // A free once these finish
+                }
+            }
+            // drain: every MMA issued by this thread finishes before TMEM is freed
             mma_commit(BAR(k, kBarDone));
             mbar_drain(BAR(k, kBarDone), 0);
         }
@@ -1001,7 +1022,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 
     tc_fence_before();
     __syncthreads();
-    if (warp == kEpiWarps) {
+    if (warp == kMmaWarp0) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
