@@ -930,32 +930,43 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) bits |= (w[i] >= thr ? 1u : 0u) << i;
                         bits &= rows;
-                        if (bits) {
+                        // append the rows whose bit is set: dense blocks with
+                        // independent predicated stores (slot = cnt + rank of the
+                        // bit), sparse ones bit by bit
+                        const int most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(bits));
+                        if (most > 0) {
+                            unsigned base;
+                            int step;
                             if constexpr (K32) {
                                 // window index of row 16b + i: (row - yr + h) * ww + (xc - xr + h)
-                                const unsigned base =
-                                    (unsigned)((T.Y0 + 16 * b - yr + G.h) * ww + (xc - xr + G.h));
-                                do {
-                                    const int i = __ffs(bits) - 1;
-                                    bits &= bits - 1;
-                                    float wi = w[0];
-#pragma unroll
-                                    for (int t = 1; t < 16; ++t) wi = i == t ? w[t] : wi;
-                                    pend32[cnt * 128] = (~orderable(wi) & ~kM) | (base + (unsigned)(i * ww));
-                                    ++cnt;
-                                } while (bits);
+                                base = (unsigned)((T.Y0 + 16 * b - yr + G.h) * ww + (xc - xr + G.h));
+                                step = ww;
                             } else {
-                                const unsigned base = (unsigned)((T.Y0 + 16 * b) * J.W + xc);
-                                do {
+                                base = (unsigned)((T.Y0 + 16 * b) * J.W + xc);
+                                step = J.W;
+                            }
+                            auto put = [&](int slot_i, float wi, int i) {
+                                if constexpr (K32)
+                                    pend32[slot_i * 128] = (~orderable(wi) & ~kM) | (base + (unsigned)(i * step));
+                                else
+                                    pend[slot_i * 128] = ((unsigned long long)__float_as_uint(wi) << 32) |
+                                                         (base + (unsigned)(i * step));
+                            };
+                            if (most > 2) {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (bits & (1u << i)) put(cnt + __popc(bits & ((1u << i) - 1u)), w[i], i);
+                                cnt += __popc(bits);
+                            } else {
+                                while (bits) {
                                     const int i = __ffs(bits) - 1;
                                     bits &= bits - 1;
                                     float wi = w[0];
 #pragma unroll
                                     for (int t = 1; t < 16; ++t) wi = i == t ? w[t] : wi;
-                                    pend[cnt * 128] = ((unsigned long long)__float_as_uint(wi) << 32) |
-                                                      (base + (unsigned)(i * J.W));
+                                    put(cnt, wi, i);
                                     ++cnt;
-                                } while (bits);
+                                }
                             }
                         }
                         // keep room for the next block's appends
