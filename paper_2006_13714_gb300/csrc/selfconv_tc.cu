@@ -610,6 +610,49 @@ __device__ void mbar_drain(uint32_t bar, uint32_t parity) {
     }
 }
 
+// A operand of a tile: reference patch rows cut from the staged tile, in the
+// canonical K-major core-matrix layout (reference m, 16-byte K chunk
+// kc = patch row u * pw + chunk q).  Shared by `nparts` threads; this one
+// takes items part, part + nparts, ...  uint8: A = 2 (x - 128), exact in
+// bf16, so the MMA gives 2 <X_r, X_j>.
+template <bool kF32>
+__device__ __forceinline__ void form_A(const TcGeom& G, const TileInfo& T, const TcJob& J,
+                                       const uint8_t* sbase, uint8_t* sa, int delta, int part,
+                                       int nparts) {
+    constexpr int nplanes = kF32 ? 2 : 1;
+    const int per_m = nplanes * G.nkc;
+    const int items = 128 * per_m;
+    for (int it = part; it < items; it += nparts) {
+        const int m = it / per_m, r = it - m * per_m;
+        const int pl = r / G.nkc, kc = r - pl * G.nkc;
+        const int u = kc / G.pw, q = kc - u * G.pw;
+        const int mw = m >> 5, ml = m & 31;
+        const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
+        const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ry < J.n_ry && rx < J.n_rx && u < G.p) {
+            const uint8_t* row = sbase + pl * G.base_bytes + (ry * G.s - T.Y0 + u) * G.base_pitch;
+            v = lds_shifted16(row, delta + (rx * G.s - T.X0) * G.Cp + 8 * q);
+            // zero the elements beyond the patch row (p * Cp elements)
+            const int valid = G.p * G.Cp - 8 * q;
+            uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (2 * i >= valid) w[i] = 0;
+                else if (2 * i + 1 >= valid) w[i] &= 0xffffu;
+                if (!kF32) {
+                    const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
+                    const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
+                    w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
+                }
+            }
+            v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        *reinterpret_cast<uint4*>(sa + pl * G.a_bytes + (m >> 3) * G.nkc * 128 + kc * 128 +
+                                  (m & 7) * 16) = v;
+    }
+}
+
 // ---------------------------------------------------------------- the kernel
 //
 // Persistent: CTA b walks the tiles b, b + G, b + 2G, ... of every job of
@@ -645,7 +688,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 mbar_init(BAR(k, kBarSEmpty + i), 1);
                 mbar_init(BAR(k, kBarFull + i), 1);
             }
-            mbar_init(BAR(k, kBarAFull), 1);
+            mbar_init(BAR(k, kBarAFull), 5);  // 4 epilogue warps + the producer
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -693,7 +736,10 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             const TileInfo T = tile_info(P, tile);
             const TcJob& J = *T.job;
             const int e0 = (T.X0 * G.Cp) & ~7, delta = T.X0 * G.Cp - e0;
-            // (1) stage the tile plus halo (this warp is done reading the previous one)
+            // (1) stage the tile plus halo: this warp is done reading the
+            // previous one, and the epilogue warps are once the previous A is formed
+            if (turn > 0 && !__all_sync(0xffffffffu, mbar_wait(BAR(k, kBarAFull), (turn - 1) & 1, abort_flag, 7)))
+                break;
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
@@ -708,45 +754,8 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             if (ok) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6));
             if (!ok) break;
             base_pending = -1;
-            // (3) A: reference patch rows cut from the staged tile; lane m
-            // takes references m, m + 32, ... (lane -> reference mapping of
-            // the epilogue), kc = patch row u, 16-byte chunk q
-            for (int m = lane; m < 128; m += 32) {
-                const int mw = m >> 5, ml = m & 31;
-                const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
-                const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
-                const bool ref_ok = ry < J.n_ry && rx < J.n_rx;
-                const int row0 = ry * G.s - T.Y0;
-                const int ecol0 = delta + (rx * G.s - T.X0) * G.Cp;
-                for (int pl = 0; pl < nplanes; ++pl) {
-                    const uint8_t* bp = sbase + pl * G.base_bytes;
-                    uint8_t* ap = sa + pl * G.a_bytes + (m >> 3) * G.nkc * 128 + (m & 7) * 16;
-                    int u = 0, q = 0;
-                    for (int kc = 0; kc < G.nkc; ++kc) {
-                        uint4 v = make_uint4(0, 0, 0, 0);
-                        if (ref_ok && u < G.p) {
-                            v = lds_shifted16(bp + (row0 + u) * G.base_pitch, ecol0 + 8 * q);
-                            // zero the elements beyond the patch row (p * Cp elements)
-                            const int valid = G.p * G.Cp - 8 * q;
-                            uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                if (2 * i >= valid) w[i] = 0;
-                                else if (2 * i + 1 >= valid) w[i] &= 0xffffu;
-                                if (!kF32) {
-                                    // uint8: A = 2 (x - 128), exact in bf16: MMA gives 2 <X_r, X_j>
-                                    const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
-                                    const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
-                                    w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
-                                }
-                            }
-                            v = make_uint4(w[0], w[1], w[2], w[3]);
-                        }
-                        *reinterpret_cast<uint4*>(ap + kc * 128) = v;
-                        if (++q == G.pw) { q = 0; ++u; }
-                    }
-                }
-            }
+            // (3) this warp's share of A (the slot's epilogue warps form the rest)
+            form_A<kF32>(G, T, J, sbase, sa, delta, 128 + lane, 160);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(BAR(k, kBarAFull));
@@ -898,6 +907,19 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             const int hi = lane_ok ? min(T.NR - 1, yr + G.h - T.Y0) : -1;
             const int* nrm_i = static_cast<const int*>(J.nrm);
             const int nr_i = (lane_ok && !kF32) ? nrm_i[(size_t)yr * J.Wc + xr] : 0;
+            // the slot's A operand (with the producer): the A region is free
+            // once the previous tile's MMAs are done, the staged tile has landed
+            if (turn > 0 && !mbar_wait(BAR(k, kBarAEmpty), (turn - 1) & 1, abort_flag, 5)) break;
+            if (!mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6)) break;
+            {
+                const int e0 = (T.X0 * G.Cp) & ~7;
+                form_A<kF32>(G, T, J, smem + G.off_slots + k * G.slot_bytes + G.off_base,
+                             smem + G.off_slots + k * G.slot_bytes + G.off_a, T.X0 * G.Cp - e0,
+                             threadIdx.x & 127, 160);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(BAR(k, kBarAFull));
+            }
             float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
             int cnt = 0;
             for (int c = 0; c < T.nchunks; ++c, ++qc) {
