@@ -50,7 +50,7 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
     // plane rows: room for the widest staged strip beyond the right edge
     g.plane_pitch = round_up(W * g.Cp + 8 * g.pw + 16, 8);
     g.plane_rows = H + g.p_eff + 8;
-    g.L = dtype == kF32 ? std::min(160, round_up(K + 16, 8)) : 0;
+    g.L = dtype == kF32 ? std::min(160, round_up(K + 8, 8)) : 0;
     return BM_OK;
 }
 

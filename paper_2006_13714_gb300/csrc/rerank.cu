@@ -28,10 +28,19 @@
 // Layout of the work: one block per tile of TRY x TRX references of one
 // image (a table of images per launch).  The block first stages the image
 // region its references' windows cover, and the norms there, in shared
-// memory, so every distance reads shared memory.  One warp per reference;
-// every ranking uses 64-bit integer keys (FP64 is slow on this part and is
-// kept to the rare boundary ties).  Shapes whose region does not fit run
-// the same steps on global memory, one image per launch.
+// memory, so every distance reads shared memory.  The region is stored as
+// element pairs (pair e of a row holds elements e and e + 1), so a patch row
+// that starts anywhere is read with 64-bit loads and its squared differences
+// are summed two at a time with packed FP32 arithmetic.  One warp per
+// reference; every ranking uses 64-bit integer keys (FP64 is slow on this
+// part and is kept to the rare boundary ties).  The block's overflow
+// references are done last by all its warps together: the (K+1)-th smallest
+// key U among the pool's direct distances bounds the keys of the window's
+// K+1 nearest, so the warps scan interleaved shares of the window and keep
+// only keys <= U (typically little more than K+1 of them), which are then
+// ranked like a band.  Should ties leave more than a buffer's worth, one
+// warp takes the window's exact top-(K+1) by insertion.  Shapes whose region
+// does not fit run the same steps on global memory, one image per launch.
 #include "bm_internal.h"
 
 #include <climits>
@@ -43,8 +52,34 @@ constexpr float kEps = 6.103515625e-05f;  // 2^-14, same constant as the tensor-
 constexpr int kFbSlots = (kMaxK + 1 + 31) / 32;
 constexpr unsigned long long kNone = ~0ull;
 constexpr int kTileWarps = 8;
+constexpr int kMaxTileRefs = 64;
+constexpr int kCandCap = kFbSlots * 32;  // window keys kept per overflow reference
 constexpr int kMaxRerankJobs = 64;
 constexpr int kTileSmemLimit = 160 * 1024;
+
+// n / d for every 32-bit n by a multiply-high and two shifts (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994;
+// the round-up method): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n).
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l > 0 ? 1 : 0;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
+    const unsigned t = __umulhi((unsigned)n, f.m);
+    return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
+}
 
 struct RerankJob {
     const float* img;
@@ -54,6 +89,7 @@ struct RerankJob {
     int32_t* out_idx;
     float* out_dist;
     int H, W, n_ry, n_rx, Hc, Wc;
+    FastDiv wdiv;  // offset -> row
     int tiles_x, tile_begin;
 };
 
@@ -62,25 +98,64 @@ struct RerankParams {
     float round_rel;  // pool-score rounding, relative: 2^(tbits - 23) (0: exact scores)
     float gamma;      // FP32 relative error bound of a direct distance
     int TRY, TRX;     // references per tile (rows, columns)
-    int img_cap;      // shared-memory image region capacity (floats); norms follow
+    int img_cap;      // shared-memory image region capacity (element pairs); norms follow
     unsigned long long* counters;  // [0] overflow, [1] fp64 rechecks, [2] bound violations
     int njobs, total_tiles;
     RerankJob jobs[kMaxRerankJobs];
 };
 
-// Pixel source: a region of the image (shared memory) or the whole image;
-// element (y, x, c) at base + (y - y0) * pitch + (x - x0) * C + c.
-struct Pix {
+// Pixel sources; element (y, x, c) of the image at elem(at(y, x), c).
+// PairSrc: a region in shared memory as element pairs {X[e], X[e + 1]}.
+struct PairSrc {
+    const float2* base;
+    int y0, x0, pitch, C;
+    __device__ __forceinline__ const float2* at(int y, int x) const {
+        return base + (y - y0) * pitch + (x - x0) * C;
+    }
+    __device__ __forceinline__ static float elem(const float2* row, int e) { return row[e].x; }
+};
+// PlainSrc: the image in global memory, or the norms region.
+struct PlainSrc {
     const float* base;
     int y0, x0, pitch, C;
     __device__ __forceinline__ const float* at(int y, int x) const {
         return base + (size_t)(y - y0) * pitch + (size_t)(x - x0) * C;
     }
+    __device__ __forceinline__ static float elem(const float* row, int e) { return row[e]; }
 };
 
-// (X_r - X_j)^2 summed row by row, elements in order (the reference's rows
-// at ref + u * pitch).
-__device__ __forceinline__ float direct_f32(const Pix& X, int p, int C, const float* ref, int yc, int xc) {
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+
+// (X_r - X_j)^2 summed over the patch (the reference's rows at
+// ref + u * pitch): elements two at a time with packed FP32 subtract and
+// fused multiply-add, even and odd elements in two running sums.
+__device__ __forceinline__ float direct_f32(const PairSrc& X, int p, int C, const float2* ref,
+                                            int yc, int xc) {
+    const int pc = p * C, np = pc >> 1;
+    unsigned long long acc = 0ull;
+    float tail = 0.f;
+    for (int u = 0; u < p; ++u) {
+        const float2* crow = X.at(yc + u, xc);
+        const float2* rrow = ref + u * X.pitch;
+#pragma unroll 4
+        for (int t = 0; t < np; ++t) {
+            unsigned long long d;
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(rrow[2 * t])), "l"(f2_bits(crow[2 * t])));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc) : "l"(d));
+        }
+        if (pc & 1) {
+            const float d = rrow[pc - 1].x - crow[pc - 1].x;
+            tail = fmaf(d, d, tail);
+        }
+    }
+    return (__uint_as_float((unsigned)acc) + __uint_as_float((unsigned)(acc >> 32))) + tail;
+}
+
+// The same sum elementwise in order (global-memory source).
+__device__ __forceinline__ float direct_f32(const PlainSrc& X, int p, int C, const float* ref,
+                                            int yc, int xc) {
     const int pc = p * C;
     float acc = 0.f;
     for (int u = 0; u < p; ++u) {
@@ -95,14 +170,15 @@ __device__ __forceinline__ float direct_f32(const Pix& X, int p, int C, const fl
     return acc;
 }
 
-__device__ __forceinline__ double direct_f64(const Pix& X, int p, int C, const float* ref, int yc, int xc) {
+template <class Src, class T>
+__device__ __forceinline__ double direct_f64(const Src& X, int p, int C, const T* ref, int yc, int xc) {
     const int pc = p * C;
     double acc = 0.0;
     for (int u = 0; u < p; ++u) {
-        const float* crow = X.at(yc + u, xc);
-        const float* rrow = ref + (size_t)u * X.pitch;
+        const T* crow = X.at(yc + u, xc);
+        const T* rrow = ref + (size_t)u * X.pitch;
         for (int e = 0; e < pc; ++e) {
-            const double d = (double)rrow[e] - (double)crow[e];
+            const double d = (double)Src::elem(rrow, e) - (double)Src::elem(crow, e);
             acc = fma(d, d, acc);
         }
     }
@@ -127,9 +203,9 @@ __device__ __forceinline__ void warp_rank(const unsigned long long (&key)[S], in
 // Final selection: members carry key (float(d32) bits << 32 | offset);
 // non-members carry kNone.  FP64 refinement at the K-th boundary, then write
 // ranks < K (and the padding).
-template <int S>
-__device__ void select_and_write(const RerankParams& P, const RerankJob& J, const Pix& X,
-                                 const float* ref, const unsigned long long (&key)[S], int nb,
+template <int S, class Src, class T>
+__device__ void select_and_write(const RerankParams& P, const RerankJob& J, const Src& X,
+                                 const T* ref, const unsigned long long (&key)[S], int nb,
                                  int lane, size_t r) {
     int rank[S];
     warp_rank(key, rank);
@@ -141,17 +217,16 @@ __device__ void select_and_write(const RerankParams& P, const RerankJob& J, cons
         d64[i] = 0.0;
     }
     if (nb > P.K) {
-        float din = 0.f, dout = 0.f;
+        unsigned din_b = 0u, dout_b = 0u;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const float d = __uint_as_float((unsigned)(key[i] >> 32));
-            if (rank[i] == P.K - 1) din = d;
-            if (rank[i] == P.K) dout = d;
+            const unsigned db = (unsigned)(key[i] >> 32);
+            if (rank[i] == P.K - 1) din_b = db;
+            if (rank[i] == P.K) dout_b = db;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            din = fmaxf(din, __shfl_xor_sync(0xffffffffu, din, o));
-            dout = fmaxf(dout, __shfl_xor_sync(0xffffffffu, dout, o));
-        }
+        // distances are non-negative: their bits order as unsigned integers
+        const float din = __uint_as_float(__reduce_max_sync(0xffffffffu, din_b));
+        const float dout = __uint_as_float(__reduce_max_sync(0xffffffffu, dout_b));
         const float tol = P.gamma * (din + dout);
         if (dout - din <= tol) {
             // boundary members: FP64 distances decide their order
@@ -161,12 +236,13 @@ __device__ void select_and_write(const RerankParams& P, const RerankJob& J, cons
                 const float d = __uint_as_float((unsigned)(key[i] >> 32));
                 if (key[i] != kNone && d >= din - 2.f * tol && d <= dout + 2.f * tol) {
                     const int off = (int)(unsigned)(key[i] & 0xffffffffu);
-                    d64[i] = direct_f64(X, P.p, P.C, ref, off / J.W, off % J.W);
+                    const int yc = fast_div(off, J.wdiv);
+                    d64[i] = direct_f64(X, P.p, P.C, ref, yc, off - yc * J.W);
                     refined[i] = true;
                     ++nrec;
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) nrec += __shfl_xor_sync(0xffffffffu, nrec, o);
+            nrec = (int)__reduce_add_sync(0xffffffffu, (unsigned)nrec);
             if (lane == 0 && nrec) atomicAdd(P.counters + 1, (unsigned long long)nrec);
             // The refined members occupy a contiguous range of ranks (they are
             // exactly the members whose FP32 distance lies in the boundary
@@ -175,7 +251,7 @@ __device__ void select_and_write(const RerankParams& P, const RerankJob& J, cons
 #pragma unroll
             for (int i = 0; i < S; ++i)
                 if (refined[i]) start = min(start, rank[i]);
-            for (int o = 16; o > 0; o >>= 1) start = min(start, __shfl_xor_sync(0xffffffffu, start, o));
+            start = __reduce_min_sync(0xffffffffu, start);
             int sub[S];
 #pragma unroll
             for (int i = 0; i < S; ++i) sub[i] = 0;
@@ -214,105 +290,166 @@ __device__ void select_and_write(const RerankParams& P, const RerankJob& J, cons
     }
 }
 
-// The steps of the file header for reference (ry, rx) of job J.  X holds
-// every pixel of the patches of its window, N (C = 1) every norm of its
-// window; list: kFbSlots * 32 words of shared memory for the overflow path.
+// The warp's pool entries of one reference (slot i holds entry lane + 32 i).
 template <int S>
-__device__ void rerank_ref(const RerankParams& P, const RerankJob& J, const Pix& X, const Pix& N,
-                           int ry, int rx, int lane, unsigned long long* list) {
-    const size_t r = (size_t)ry * J.n_rx + rx;
-    const int yr = ry * P.s, xr = rx * P.s;
-    const float* ref = X.at(yr, xr);  // reference rows at ref + u * X.pitch
-    const float nr = *N.at(yr, xr);
-
-    // ---- load the pool (best first; empty slots have offset -1)
-    float v[S], nc[S];
+struct PoolRegs {
     int off[S];
-    int npool = 0;
+    float v[S];
+    __device__ __forceinline__ void load(const RerankParams& P, const RerankJob& J, size_t r, int lane) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-        const int k = lane + 32 * i;
-        v[i] = -__int_as_float(0x7f800000);
-        off[i] = -1;
-        nc[i] = 0.f;
-        if (k < P.L) {
-            off[i] = J.pool_idx[r * P.L + k];
-            if (off[i] >= 0) {
-                v[i] = J.pool_score[r * P.L + k];
-                nc[i] = *N.at(off[i] / J.W, off[i] % J.W);
-                ++npool;
+        for (int i = 0; i < S; ++i) {
+            const int k = lane + 32 * i;
+            off[i] = -1;
+            v[i] = 0.f;
+            if (k < P.L) {
+                off[i] = __ldg(J.pool_idx + r * P.L + k);
+                v[i] = __ldg(J.pool_score + r * P.L + k);
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) npool += __shfl_xor_sync(0xffffffffu, npool, o);
+};
+
+// Steps 1, 2 and 4 of the file header for reference (ry, rx) of job J, and
+// step 3 with the output unless the band overflows.  X holds every pixel of
+// the patches of its window, N (C = 1) every norm of its window.  Returns
+// true on overflow: nothing is written and U is the (K+1)-th smallest key of
+// the pool's direct distances (the window is recomputed).
+template <int S, class Src, class T>
+__device__ bool rerank_ref(const RerankParams& P, const RerankJob& J, const Src& X, const PlainSrc& N,
+                           int ry, int rx, int lane, const PoolRegs<S>& pool, unsigned long long& U) {
+    const size_t r = (size_t)ry * J.n_rx + rx;
+    const int yr = ry * P.s, xr = rx * P.s;
+    const T* ref = X.at(yr, xr);  // reference rows at ref + u * X.pitch
+    const float nr = *N.at(yr, xr);
+
+    // ---- the pool (best first; empty slots have offset -1)
+    float v[S], nc[S];
+    int yc[S], xc[S];
+    int npool = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        const int off = pool.off[i];
+        v[i] = -__int_as_float(0x7f800000);
+        nc[i] = 0.f;
+        yc[i] = 0;
+        xc[i] = 0;
+        if (off >= 0) {
+            yc[i] = fast_div(off, J.wdiv);
+            xc[i] = off - yc[i] * J.W;
+            v[i] = pool.v[i];
+            nc[i] = *N.at(yc[i], xc[i]);
+        }
+        npool += __popc(__ballot_sync(0xffffffffu, off >= 0));
+    }
 
     // ---- band: entries with v >= tb (see the file header); the pool is
     // sorted, so the K-th largest score is entry K-1
     bool member[S];
 #pragma unroll
-    for (int i = 0; i < S; ++i) member[i] = off[i] >= 0;
+    for (int i = 0; i < S; ++i) member[i] = pool.off[i] >= 0;
     int nb = npool;
     bool overflow = false;
     if (npool > P.K) {
-        float vK = -__int_as_float(0x7f800000), ncmax = 0.f, vabs = 0.f;
+        float vK = 0.f;
+        unsigned ncmax = 0u, vabs = 0u;  // bits of non-negative floats order as integers
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             const int k = lane + 32 * i;
-            if (k == P.K - 1) vK = v[i];
+            const float vs = __shfl_sync(0xffffffffu, v[i], (P.K - 1) & 31);
+            if (i == (P.K - 1) >> 5) vK = vs;
             if (k < P.K) {
-                ncmax = fmaxf(ncmax, nc[i]);
-                vabs = fmaxf(vabs, fabsf(v[i]));
+                ncmax = max(ncmax, __float_as_uint(nc[i]));
+                vabs = max(vabs, __float_as_uint(fabsf(v[i])));
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            vK = fmaxf(vK, __shfl_xor_sync(0xffffffffu, vK, o));
-            ncmax = fmaxf(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
-            vabs = fmaxf(vabs, __shfl_xor_sync(0xffffffffu, vabs, o));
-        }
-        const float tb = vK - P.round_rel * vabs * 1.001f - 2.0f * kEps * (nr + ncmax) * 1.0001f;
+        const float ncm = __uint_as_float(__reduce_max_sync(0xffffffffu, ncmax));
+        const float va = __uint_as_float(__reduce_max_sync(0xffffffffu, vabs));
+        const float tb = vK - P.round_rel * va * 1.001f - 2.0f * kEps * (nr + ncm) * 1.0001f;
         int cnt = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            member[i] = off[i] >= 0 && v[i] >= tb;
-            cnt += member[i] ? 1 : 0;
+            member[i] = pool.off[i] >= 0 && v[i] >= tb;
+            cnt += __popc(__ballot_sync(0xffffffffu, member[i]));
         }
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         nb = cnt;
         overflow = (npool == P.L) && (nb == P.L);
     }
 
-    if (!overflow) {
-        unsigned long long key[S];
-        int viol = 0;
+    unsigned long long key[S];
+    int viol = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        key[i] = kNone;
+        if (member[i]) {
+            const float d32 = direct_f32(X, P.p, P.C, ref, yc[i], xc[i]);
+            key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)pool.off[i];
+            // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
+            const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
+            if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + 2.0f * P.round_rel * fabsf(v[i]) +
+                                      P.gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
+                ++viol;
+        }
+    }
+    viol = (int)__reduce_add_sync(0xffffffffu, (unsigned)viol);
+    if (lane == 0 && viol) atomicAdd(P.counters + 2, (unsigned long long)viol);
+    if (overflow) {
+        // every entry is a member (L > K): the key of rank K exists and is unique
+        int rank[S];
+        warp_rank(key, rank);
+        U = kNone;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            key[i] = kNone;
-            if (member[i]) {
-                const float d32 = direct_f32(X, P.p, P.C, ref, off[i] / J.W, off[i] % J.W);
-                key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)off[i];
-                // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
-                const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
-                if (fabsf(dt - d32) > 2.0f * kEps * (nr + nc[i]) + 2.0f * P.round_rel * fabsf(v[i]) +
-                                          P.gamma * d32 + 1e-6f * (nr + nc[i]) + 1.0f)
-                    ++viol;
-            }
+            const unsigned b = __ballot_sync(0xffffffffu, rank[i] == P.K);
+            if (b) U = __shfl_sync(0xffffffffu, key[i], __ffs(b) - 1);
         }
-        for (int o = 16; o > 0; o >>= 1) viol += __shfl_xor_sync(0xffffffffu, viol, o);
-        if (lane == 0 && viol) atomicAdd(P.counters + 2, (unsigned long long)viol);
-        select_and_write<S>(P, J, X, ref, key, nb, lane, r);
-        return;
+        return true;
     }
+    select_and_write<S>(P, J, X, ref, key, nb, lane, r);
+    return false;
+}
 
-    // ---- overflow: exact top-(K+1) over the whole window, FP32 direct distances
-    if (lane == 0) atomicAdd(P.counters + 0, 1ull);
+// Inserts the warp's keys k (one per lane) into the sorted list of nl keys
+// in shared memory (kNone-padded), keeping the nl smallest.
+__device__ __forceinline__ void list_insert(unsigned long long k, unsigned long long* list, int nl,
+                                            int lane) {
+    unsigned pass = __ballot_sync(0xffffffffu, k < list[nl - 1]);
+    while (pass) {
+        const int src = __ffs(pass) - 1;
+        pass &= pass - 1;
+        const unsigned long long kk = __shfl_sync(0xffffffffu, k, src);
+        if (!(kk < list[nl - 1])) continue;
+        int pos = 0;
+        for (int e = lane; e < nl; e += 32) pos += list[e] < kk ? 1 : 0;
+        pos = (int)__reduce_add_sync(0xffffffffu, (unsigned)pos);
+        unsigned long long nv[kFbSlots];
+#pragma unroll
+        for (int t = 0; t < kFbSlots; ++t) {
+            const int e = lane + 32 * t;
+            nv[t] = e < nl ? (e > pos ? list[e - 1] : (e == pos ? kk : list[e])) : kNone;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kFbSlots; ++t)
+            if (lane + 32 * t < nl) list[lane + 32 * t] = nv[t];
+        __syncwarp();
+    }
+}
+
+// Overflow, share `part` of `nparts`: the exact top-(K+1) of the window
+// candidates 32 part + lane + 32 nparts m (FP32 direct distances) into list.
+template <class Src, class T>
+__device__ void window_part(const RerankParams& P, const RerankJob& J, const Src& X, int ry, int rx,
+                            int part, int nparts, int lane, unsigned long long* list) {
     const int nl = P.K + 1;
+    const int yr = ry * P.s, xr = rx * P.s;
+    const T* ref = X.at(yr, xr);
     for (int e = lane; e < kFbSlots * 32; e += 32) list[e] = kNone;
     __syncwarp();
     const int y0 = max(0, yr - P.h), y1 = min(J.Hc - 1, yr + P.h);
     const int x0 = max(0, xr - P.h), x1 = min(J.Wc - 1, xr + P.h);
     const int nxw = x1 - x0 + 1;
     const int total = (y1 - y0 + 1) * nxw;
-    for (int base = 0; base < total; base += 32) {
+    for (int base = part * 32; base < total; base += 32 * nparts) {
         const int i = base + lane;
         unsigned long long k = kNone;
         if (i < total) {
@@ -320,38 +457,49 @@ __device__ void rerank_ref(const RerankParams& P, const RerankJob& J, const Pix&
             const float d = direct_f32(X, P.p, P.C, ref, yc, xc);
             k = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * J.W + xc);
         }
-        unsigned pass = __ballot_sync(0xffffffffu, k < list[nl - 1]);
-        while (pass) {
-            const int src = __ffs(pass) - 1;
-            pass &= pass - 1;
-            const unsigned long long kk = __shfl_sync(0xffffffffu, k, src);
-            if (!(kk < list[nl - 1])) continue;
-            int pos = 0;
-            for (int e = lane; e < nl; e += 32) pos += list[e] < kk ? 1 : 0;
-            for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
-            unsigned long long nv[kFbSlots];
-#pragma unroll
-            for (int t = 0; t < kFbSlots; ++t) {
-                const int e = lane + 32 * t;
-                nv[t] = e < nl ? (e > pos ? list[e - 1] : (e == pos ? kk : list[e])) : kNone;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < kFbSlots; ++t)
-                if (lane + 32 * t < nl) list[lane + 32 * t] = nv[t];
-            __syncwarp();
+        list_insert(k, list, nl, lane);
+    }
+}
+
+// Overflow, share `part` of `nparts` of the window (candidates
+// 32 part + lane + 32 nparts m): FP32 direct-distance keys <= U appended to
+// cand (slots past kCandCap are counted but not stored).
+template <class Src, class T>
+__device__ void window_filter(const RerankParams& P, const RerankJob& J, const Src& X, int ry, int rx,
+                              int part, int nparts, int lane, unsigned long long U,
+                              unsigned long long* cand, int* cand_n) {
+    const int yr = ry * P.s, xr = rx * P.s;
+    const T* ref = X.at(yr, xr);
+    const int y0 = max(0, yr - P.h), y1 = min(J.Hc - 1, yr + P.h);
+    const int x0 = max(0, xr - P.h), x1 = min(J.Wc - 1, xr + P.h);
+    const int nxw = x1 - x0 + 1;
+    const int total = (y1 - y0 + 1) * nxw;
+    for (int i = part * 32 + lane; i < total; i += 32 * nparts) {
+        const int yc = y0 + i / nxw, xc = x0 + i % nxw;
+        const float d = direct_f32(X, P.p, P.C, ref, yc, xc);
+        const unsigned long long k = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(yc * J.W + xc);
+        if (k <= U) {
+            const int slot = atomicAdd(cand_n, 1);
+            if (slot < kCandCap) cand[slot] = k;
         }
     }
+}
+
+// The list's keys through select_and_write.
+template <class Src, class T>
+__device__ void write_list(const RerankParams& P, const RerankJob& J, const Src& X, int ry, int rx,
+                           int lane, const unsigned long long* list) {
+    const int nl = P.K + 1;
     unsigned long long key2[kFbSlots];
     int cnt = 0;
 #pragma unroll
     for (int t = 0; t < kFbSlots; ++t) {
         const int e = lane + 32 * t;
         key2[t] = e < nl ? list[e] : kNone;
-        cnt += key2[t] != kNone ? 1 : 0;
+        cnt += __popc(__ballot_sync(0xffffffffu, key2[t] != kNone));
     }
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    select_and_write<kFbSlots>(P, J, X, ref, key2, cnt, lane, r);
+    const T* ref = X.at(ry * P.s, rx * P.s);
+    select_and_write<kFbSlots>(P, J, X, ref, key2, cnt, lane, (size_t)ry * J.n_rx + rx);
 }
 
 // Tile t of the launch: its job (binary search over the jobs' first tiles).
@@ -367,37 +515,97 @@ __device__ __forceinline__ int tile_job(const RerankParams& P, int t) {
 
 template <int S>
 __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
-    extern __shared__ __align__(16) float sm[];
-    __shared__ unsigned long long list_s[kTileWarps][kFbSlots * 32];
+    extern __shared__ __align__(16) float2 sm2[];
+    __shared__ unsigned long long list_s[kFbSlots * 32];  // overflow: window keys, then a list
+    __shared__ unsigned long long ovf_u[kMaxTileRefs];
+    __shared__ int ovf_ref[kMaxTileRefs];
+    __shared__ int ovf_n, cand_n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x;
     const RerankJob& J = P.jobs[tile_job(P, t)];
     const int lt = t - J.tile_begin;
     const int ry0 = (lt / J.tiles_x) * P.TRY, rx0 = (lt % J.tiles_x) * P.TRX;
     const int ry1 = min(ry0 + P.TRY, J.n_ry) - 1, rx1 = min(rx0 + P.TRX, J.n_rx) - 1;
+    const int ncols = rx1 - rx0 + 1;
+    const int nref = (ry1 - ry0 + 1) * ncols;
+    // the warp's first pool, in flight while the region is staged
+    PoolRegs<S> pool;
+    if (warp < nref) pool.load(P, J, (size_t)(ry0 + warp / ncols) * J.n_rx + rx0 + warp % ncols, lane);
+    if (threadIdx.x == 0) ovf_n = 0;
     // region: every pixel of every window patch of the tile's references
     const int iy0 = max(0, ry0 * P.s - P.h), iy1 = min(J.H - 1, ry1 * P.s + P.h + P.p - 1);
     const int ix0 = max(0, rx0 * P.s - P.h), ix1 = min(J.W - 1, rx1 * P.s + P.h + P.p - 1);
     const int ny1 = min(J.Hc - 1, ry1 * P.s + P.h), nx1 = min(J.Wc - 1, rx1 * P.s + P.h);
     const int ipitch = (ix1 - ix0 + 1) * P.C, npitch = nx1 - ix0 + 1;
-    float* simg = sm;
-    float* snrm = sm + P.img_cap;
+    float2* simg = sm2;
+    float* snrm = reinterpret_cast<float*>(sm2 + P.img_cap);
     const int irows = iy1 - iy0 + 1, nrows = ny1 - iy0 + 1;
-    for (int i = threadIdx.x; i < irows * ipitch; i += blockDim.x) {
-        const int y = i / ipitch, e = i % ipitch;
-        simg[i] = __ldg(J.img + ((size_t)(iy0 + y) * J.W + ix0) * P.C + e);
+    for (int y = warp; y < irows; y += kTileWarps) {
+        const float* g = J.img + ((size_t)(iy0 + y) * J.W + ix0) * P.C;
+        for (int e0 = 0; e0 < ipitch; e0 += 32) {
+            const int e = e0 + lane;
+            const float a = e < ipitch ? __ldg(g + e) : 0.f;
+            float b = __shfl_down_sync(0xffffffffu, a, 1);
+            if (lane == 31) b = e + 1 < ipitch ? __ldg(g + e + 1) : 0.f;
+            if (e < ipitch) simg[y * ipitch + e] = make_float2(a, b);
+        }
     }
-    for (int i = threadIdx.x; i < nrows * npitch; i += blockDim.x) {
-        const int y = i / npitch, x = i % npitch;
-        snrm[i] = __ldg(J.nrm + (size_t)(iy0 + y) * J.Wc + ix0 + x);
+    for (int y = warp; y < nrows; y += kTileWarps) {
+        const float* g = J.nrm + (size_t)(iy0 + y) * J.Wc + ix0;
+        for (int x = lane; x < npitch; x += 32) snrm[y * npitch + x] = __ldg(g + x);
     }
     __syncthreads();
-    const Pix X{simg, iy0, ix0, ipitch, P.C};
-    const Pix N{snrm, iy0, ix0, npitch, 1};
-    const int ncols = rx1 - rx0 + 1;
-    const int nref = (ry1 - ry0 + 1) * ncols;
-    for (int i = warp; i < nref; i += kTileWarps)
-        rerank_ref<S>(P, J, X, N, ry0 + i / ncols, rx0 + i % ncols, lane, list_s[warp]);
+    const PairSrc X{simg, iy0, ix0, ipitch, P.C};
+    const PlainSrc N{snrm, iy0, ix0, npitch, 1};
+    // references i = warp + 8 m, row-major in the tile: (qi, ri) = divmod(i, ncols)
+    int qi = warp / ncols, ri = warp % ncols;
+    for (int i = warp; i < nref; i += kTileWarps) {
+        const PoolRegs<S> cur = pool;
+        const int ry = ry0 + qi, rx = rx0 + ri;
+        ri += kTileWarps;
+        while (ri >= ncols) {
+            ri -= ncols;
+            ++qi;
+        }
+        if (i + kTileWarps < nref) pool.load(P, J, (size_t)(ry0 + qi) * J.n_rx + rx0 + ri, lane);
+        unsigned long long U;
+        if (rerank_ref<S, PairSrc, float2>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
+            const int o = atomicAdd(&ovf_n, 1);
+            ovf_ref[o] = i;
+            ovf_u[o] = U;
+        }
+    }
+    __syncthreads();
+    // overflow references: every warp filters a share of the window by U
+    const int novf = ovf_n;
+    for (int o = 0; o < novf; ++o) {
+        const int i = ovf_ref[o];
+        const int ry = ry0 + i / ncols, rx = rx0 + i % ncols;
+        if (threadIdx.x == 0) {
+            cand_n = 0;
+            atomicAdd(P.counters + 0, 1ull);
+        }
+        __syncthreads();
+        window_filter<PairSrc, float2>(P, J, X, ry, rx, warp, kTileWarps, lane, ovf_u[o], list_s, &cand_n);
+        __syncthreads();
+        const int n = cand_n;
+        if (warp == 0) {
+            if (n <= kCandCap) {
+                unsigned long long key[kFbSlots];
+#pragma unroll
+                for (int t = 0; t < kFbSlots; ++t)
+                    key[t] = lane + 32 * t < n ? list_s[lane + 32 * t] : kNone;
+                __syncwarp();
+                select_and_write<kFbSlots>(P, J, X, X.at(ry * P.s, rx * P.s), key, n, lane,
+                                           (size_t)ry * J.n_rx + rx);
+            } else {
+                // more ties than the buffer holds: the exact top-(K+1) by insertion
+                window_part<PairSrc, float2>(P, J, X, ry, rx, 0, 1, lane, list_s);
+                write_list<PairSrc, float2>(P, J, X, ry, rx, lane, list_s);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // The same steps on global memory: one image, one reference per warp.
@@ -408,9 +616,17 @@ __global__ void __launch_bounds__(128) rerank_global_kernel(const __grid_constan
     const RerankJob& J = P.jobs[0];
     const size_t r = (size_t)blockIdx.x * 4 + warp;
     if (r >= (size_t)J.n_ry * J.n_rx) return;
-    const Pix X{J.img, 0, 0, J.W * P.C, P.C};
-    const Pix N{J.nrm, 0, 0, J.Wc, 1};
-    rerank_ref<S>(P, J, X, N, (int)(r / J.n_rx), (int)(r % J.n_rx), lane, list_s[warp]);
+    const PlainSrc X{J.img, 0, 0, J.W * P.C, P.C};
+    const PlainSrc N{J.nrm, 0, 0, J.Wc, 1};
+    const int ry = (int)(r / J.n_rx), rx = (int)(r % J.n_rx);
+    PoolRegs<S> pool;
+    pool.load(P, J, r, lane);
+    unsigned long long U;
+    if (rerank_ref<S, PlainSrc, float>(P, J, X, N, ry, rx, lane, pool, U)) {
+        if (lane == 0) atomicAdd(P.counters + 0, 1ull);
+        window_part<PlainSrc, float>(P, J, X, ry, rx, 0, 1, lane, list_s[warp]);
+        write_list<PlainSrc, float>(P, J, X, ry, rx, lane, list_s[warp]);
+    }
 }
 
 // Tile shape and shared memory for a class; false: no region fits.
@@ -419,8 +635,8 @@ bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
     for (const auto& sh : kShapes) {
         const int rows = (sh[0] - 1) * g.s + 2 * g.h + g.p;
         const int cols = (sh[1] - 1) * g.s + 2 * g.h + g.p;
-        img_cap = (rows * cols * g.C + 3) / 4 * 4;
-        smem = (img_cap + rows * cols) * 4;
+        img_cap = (rows * cols * g.C + 1) / 2 * 2;  // element pairs (8 B each)
+        smem = img_cap * 8 + (rows - g.p + 1) * (cols - g.p + 1) * 4;
         if (smem <= kTileSmemLimit) {
             TRY = sh[0];
             TRX = sh[1];
@@ -446,6 +662,7 @@ RerankJob make_job(const Geom& g, const RerankArgs& a) {
     j.img = a.img; j.nrm = a.nrm; j.pool_idx = a.pool_idx; j.pool_score = a.pool_score;
     j.out_idx = a.out_idx; j.out_dist = a.out_dist;
     j.H = g.H; j.W = g.W; j.n_ry = g.n_ry; j.n_rx = g.n_rx; j.Hc = g.Hc; j.Wc = g.Wc;
+    j.wdiv = make_fastdiv((unsigned)g.W);
     return j;
 }
 
