@@ -418,7 +418,9 @@ __device__ __forceinline__ void bitonic_merge(T (&v)[N]) {
 // arrive in batches of kBatch: the batch is bitonic-sorted, the LC smallest
 // of list + batch are min(a[i], batch[LC-1-i]) (a bitonic sequence), and one
 // bitonic merge restores the order -- far fewer compare-exchanges per key
-// than a full insertion pass per key.  Entries 0..cap-1 are the
+// than a full insertion pass per key.  LC = 24 (not a power of two) runs
+// the 32-wide bitonic merge of list ++ reversed batch with the comparators
+// that cannot change the 24 smallest left out.  Entries 0..cap-1 are the
 // answer (cap <= LC); extra entries only make the list a superset.
 template <int LC, class T = unsigned long long>
 struct RegTopK {
@@ -431,12 +433,46 @@ struct RegTopK {
     }
     __device__ __forceinline__ void merge_batch(T (&b)[kBatch]) {
         bitonic_sort<kBatch>(b);
+        if constexpr (LC == 24) {
+            static_assert(kBatch == 8, "the 24-entry merge takes batches of 8");
+            // c = a[0..23] ++ (b descending) is bitonic.  Half-cleaner (i, i+16):
+            // for i < 8 both are sorted list entries (no exchange); for i >= 8
+            // the partner is batch entry 7 - (i - 8)
 #pragma unroll
-        for (int i = 0; i < LC; ++i) {
-            const int bi = LC - 1 - i;
-            if (bi < kBatch) a[i] = b[bi] < a[i] ? b[bi] : a[i];
+            for (int i = 8; i < 16; ++i) {
+                T& hi = b[15 - i];
+                const T lo = min(a[i], hi);
+                hi = max(a[i], hi);
+                a[i] = lo;
+            }
+            // lower half c[0..15] = a[0..15]: bitonic, sorted by a 16-wide merge;
+            // upper half c[16..31] = a[16..23] ++ (b[7..0]): only its 8 smallest
+            // are kept -- half-cleaner (16+i, 24+i), then an 8-wide merge
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[16 + i] = min(a[16 + i], b[7 - i]);
+            T lo16[16], hi8[8];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) lo16[i] = a[i];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hi8[i] = a[16 + i];
+            bitonic_merge<16>(lo16);
+            bitonic_merge<8>(hi8);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = lo16[i];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[16 + i] = hi8[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < LC; ++i) {
+                const int bi = LC - 1 - i;
+                if (bi < kBatch) a[i] = b[bi] < a[i] ? b[bi] : a[i];
+            }
+            bitonic_merge<LC>(a);
         }
-        bitonic_merge<LC>(a);
+    }
+    __device__ __forceinline__ T last() const {  // entry cap-1
+        if (cap == LC) return a[LC - 1];
+        return kth();
     }
     __device__ __forceinline__ T kth() const {  // entry cap-1
         T r = 0;
@@ -454,8 +490,9 @@ struct RegTopK {
 // compare-exchange.  The cleared bits round v up by less than 2^tbits ulp
 // (v' = from_orderable(~(key & ~M)) >= v); the re-rank widens its band by
 // that amount.
+template <int LC>
 __device__ __forceinline__ void merge_pending32(unsigned* pend, int& cnt, float& thr,
-                                                RegTopK<32, unsigned>& reg, unsigned M) {
+                                                RegTopK<LC, unsigned>& reg, unsigned M) {
     const int m = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
     for (int j0 = 0; j0 < m; j0 += kBatch) {
         unsigned b[kBatch];
@@ -464,12 +501,13 @@ __device__ __forceinline__ void merge_pending32(unsigned* pend, int& cnt, float&
         reg.merge_batch(b);
     }
     cnt = 0;
-    const unsigned t = reg.kth();
+    const unsigned t = reg.last();
     // lowest value whose key can still beat the list's last entry
     if (t != ~0u) thr = from_orderable(~(t | M));
 }
-__device__ __noinline__ RegTopK<32, unsigned> final_merge32(unsigned* pend, int cnt,
-                                                            RegTopK<32, unsigned> reg, unsigned M) {
+template <int LC>
+__device__ __noinline__ RegTopK<LC, unsigned> final_merge32(unsigned* pend, int cnt,
+                                                            RegTopK<LC, unsigned> reg, unsigned M) {
     float thr = 0.f;
     merge_pending32(pend, cnt, thr, reg, M);
     return reg;
@@ -511,7 +549,7 @@ __device__ __forceinline__ void merge_pending(const TcGeom& G, const int* nrm_i,
     }
     cnt = 0;
     unsigned long long t;
-    if constexpr (LC > 0) t = reg.kth();
+    if constexpr (LC > 0) t = reg.last();
     else t = heap.top();
     if (t != kEmpty) {
         if (kF32) thr = from_orderable(~(unsigned)(t >> 32));
@@ -892,7 +930,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             const TileInfo T = tile_info(P, tile);
             const TcJob& J = *T.job;
             RegTopK<LC == 0 ? 1 : LC> reg;
-            RegTopK<32, unsigned> reg32;
+            RegTopK<K32 ? LC : 32, unsigned> reg32;
             if constexpr (K32) reg32.init(G.HL);
             else reg.init(G.HL);
             if constexpr (LC == 0) {
@@ -1027,7 +1065,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 };
                 if constexpr (K32) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
+                    for (int i = 0; i < LC; ++i) {
                         if (i < nout) {
                             const unsigned key = reg32.a[i];
                             int32_t off = -1;
@@ -1226,12 +1264,14 @@ cudaError_t launch_params(TcParams& P, cudaStream_t st) {
     int threads;
     if (T.nslots == 2) {
         threads = cta_threads(2);
-        if (T.f32) kern = T.tbits ? tc_match_kernel<32, true, 2, true> : tc_match_kernel<32, true, 2, false>;
+        if (T.f32) kern = !T.tbits ? tc_match_kernel<32, true, 2, false>
+                          : T.HL <= 24 ? tc_match_kernel<24, true, 2, true> : tc_match_kernel<32, true, 2, true>;
         else kern = T.HL <= 16 ? tc_match_kernel<16, false, 2, false> : tc_match_kernel<32, false, 2, false>;
     } else {
         threads = cta_threads(1);
         if (T.f32) kern = T.HL > 32 ? tc_match_kernel<0, true, 1, false>
-                        : T.tbits ? tc_match_kernel<32, true, 1, true> : tc_match_kernel<32, true, 1, false>;
+                        : !T.tbits ? tc_match_kernel<32, true, 1, false>
+                        : T.HL <= 24 ? tc_match_kernel<24, true, 1, true> : tc_match_kernel<32, true, 1, true>;
         else kern = T.HL <= 16 ? tc_match_kernel<16, false, 1, false>
                   : T.HL <= 32 ? tc_match_kernel<32, false, 1, false> : tc_match_kernel<0, false, 1, false>;
     }

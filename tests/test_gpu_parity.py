@@ -82,6 +82,20 @@ def test_constant_image_tie_break(ctx, algo, dt):
     compare(img, 6, 9, 2, 30, gidx, gdist)
 
 
+@pytest.mark.parametrize("sigma", [0.05, 0.0])
+def test_float_band_overflow_matches_oracle(ctx, sigma):
+    # binary texture: patch distances cluster at multiples of 255^2, so the
+    # error band around the K-th pool score holds the whole pool and the
+    # re-rank recomputes those windows (sigma 0: exact ties, broken by offset)
+    rng = np.random.default_rng(321)
+    img = (255.0 * (rng.random((56, 60)) < 0.5) +
+           sigma * rng.standard_normal((56, 60))).astype(np.float32)
+    before = ctx.stats()["rerank_overflow"]
+    gidx, gdist = run(ctx, img, 8, 21, 2, 16, "selfconv")
+    assert ctx.stats()["rerank_overflow"] > before
+    compare(img, 8, 21, 2, 16, gidx, gdist)
+
+
 FULL = [
     ("cfg2_512_f32", 512, 512, 1, "f32", 8, 39, 3, 16, 2000),
     ("cfg4_1024x4_u8", 1024, 1024, 4, "u8", 8, 39, 3, 32, 4000),
