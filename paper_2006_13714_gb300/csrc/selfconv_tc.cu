@@ -64,6 +64,7 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kBatch = 8;  // keys merged into the register list at a time
+constexpr int kMergeAt = 12;  // merge once a lane holds this many pending keys
 constexpr int kMaxSt = 3;  // stages per slot (upper bound)
 
 // Threads of a CTA with NS slots: 4 epilogue warps, 1 producer warp and 1
@@ -960,6 +961,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             }
             float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
             int cnt = 0;
+            const int merge_at = min(kMergeAt, G.kbuf - 15);  // room for one more block
             for (int c = 0; c < T.nchunks; ++c, ++qc) {
                 const int buf = qc & 1, ub = qc >> 1;
                 if (!mbar_wait(BAR(k, kBarTFull + buf), ub & 1, abort_flag, 4)) break;
@@ -990,9 +992,9 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) bits |= (w[i] >= thr ? 1u : 0u) << i;
                         bits &= rows;
-                        // append the rows whose bit is set: dense blocks with
-                        // independent predicated stores (slot = cnt + rank of the
-                        // bit), sparse ones bit by bit
+                        // append the rows whose bit is set: dense blocks with one
+                        // predicated store per row, sparse ones bit by bit (the
+                        // row's value picked by a 4-level select tree on its index)
                         const int most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(bits));
                         if (most > 0) {
                             unsigned base;
@@ -1012,25 +1014,30 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                                     pend[slot_i * 128] = ((unsigned long long)__float_as_uint(wi) << 32) |
                                                          (base + (unsigned)(i * step));
                             };
-                            if (most > 2) {
+                            if (most > 4) {
 #pragma unroll
-                                for (int i = 0; i < 16; ++i)
-                                    if (bits & (1u << i)) put(cnt + __popc(bits & ((1u << i) - 1u)), w[i], i);
-                                cnt += __popc(bits);
+                                for (int i = 0; i < 16; ++i) {
+                                    if (bits & (1u << i)) put(cnt, w[i], i);
+                                    cnt += (bits >> i) & 1u;
+                                }
                             } else {
                                 while (bits) {
                                     const int i = __ffs(bits) - 1;
                                     bits &= bits - 1;
-                                    float wi = w[0];
+                                    float s8[8], s4[4], s2[2];
 #pragma unroll
-                                    for (int t = 1; t < 16; ++t) wi = i == t ? w[t] : wi;
-                                    put(cnt, wi, i);
+                                    for (int t = 0; t < 8; ++t) s8[t] = (i & 1) ? w[2 * t + 1] : w[2 * t];
+#pragma unroll
+                                    for (int t = 0; t < 4; ++t) s4[t] = (i & 2) ? s8[2 * t + 1] : s8[2 * t];
+#pragma unroll
+                                    for (int t = 0; t < 2; ++t) s2[t] = (i & 4) ? s4[2 * t + 1] : s4[2 * t];
+                                    put(cnt, (i & 8) ? s2[1] : s2[0], i);
                                     ++cnt;
                                 }
                             }
                         }
                         // keep room for the next block's appends
-                        if (__any_sync(0xffffffffu, cnt > G.kbuf - 16)) {
+                        if (__any_sync(0xffffffffu, cnt >= merge_at)) {
                             if constexpr (K32) merge_pending32(pend32, cnt, thr, reg32, kM);
                             else merge_pending<LC, kF32, 128>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
                         }
