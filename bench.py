@@ -307,6 +307,48 @@ def serve_latency(ctx, pkg, synth, dev, n=160, seed=SEED_BASE + 55):
                         "sides 128-768 (seeded)"}
 
 
+def groups_throughput(ctx, imgs, outs, peaks, stream, dev, n=16):
+    """Patch-group gather and reconstruction (the steps on either side of the
+    matching, §IV) on n images of the workload, from their matches: CUDA
+    events on the launch stream; every image's groups are written before the
+    first is read back, so the reconstruction reads them from HBM."""
+    import torch
+    H, W, p, s, K = WL["H"], WL["W"], WL["patch"], WL["stride"], WL["K"]
+    ny, nx = (H - p) // s + 1, (W - p) // s + 1
+    n = min(n, len(imgs))
+    gbufs = [torch.empty((ny * nx, K, p * p), dtype=torch.float32, device=dev) for _ in range(n)]
+    obufs = [(torch.empty((H, W, 1), dtype=torch.float32, device=dev),
+              torch.empty((H, W), dtype=torch.float32, device=dev)) for _ in range(n)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    times = []
+    for rep in range(4):  # 1 warm-up + 3 timed
+        e[0].record(stream)
+        for i in range(n):
+            ctx.gather_groups(imgs[i], p, outs[i][0], ny, nx, out=gbufs[i], stream=stream)
+        e[1].record(stream)
+        for i in range(n):
+            ctx.aggregate(gbufs[i], outs[i][0], H, W, 1, p, ny, nx, out=obufs[i], stream=stream)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        if rep:
+            times.append((e[0].elapsed_time(e[1]) / n, e[1].elapsed_time(e[2]) / n))
+    g_ms = min(t[0] for t in times)
+    a_ms = min(t[1] for t in times)
+    group_bytes = ny * nx * K * p * p * 4
+    idx_bytes = ny * nx * K * 4
+    g_alg = group_bytes + idx_bytes + H * W * 4           # write groups, read idx + image
+    a_alg = group_bytes + idx_bytes + H * W * 4 * 2       # read groups + idx, write image + weights
+    peak = peaks.get("hbm_gbs")
+    gbs_g, gbs_a = g_alg / (g_ms / 1e3) / 1e9, a_alg / (a_ms / 1e3) / 1e9
+    return {"images": n, "gather_us_per_image": 1e3 * g_ms, "aggregate_us_per_image": 1e3 * a_ms,
+            "gather_bytes_per_image": g_alg, "aggregate_bytes_per_image": a_alg,
+            "gather_GBps": gbs_g, "aggregate_GBps": gbs_a,
+            "hbm_peak_GBps": peak, "peak_source": "of measured (copy)" if peak else None,
+            "gather_frac": gbs_g / peak if peak else None,
+            "aggregate_frac": gbs_a / peak if peak else None,
+            "groups_per_image": ny * nx, "layout": "float32 [refs][K][p*p]"}
+
+
 def run_ours(args, world, rank, local, dist):
     import torch
     import paper_2006_13714_gb300 as pkg
@@ -443,6 +485,7 @@ def run_ours(args, world, rank, local, dist):
     e2e_value = nR * n_e2e * e2e_steps * world / e2e_s
 
     serve = serve_latency(ctx, pkg, synth, dev) if not args.no_serve else None
+    groups = groups_throughput(ctx, imgs, outs, peaks, stream, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -475,6 +518,7 @@ def run_ours(args, world, rank, local, dist):
         "stage_ms_share": stage_share,
         "kernel_ms_per_step_with_stage_events": staged_ms,
         "serve": serve,
+        "groups": groups,
         "direct_fp32_gpu": {"ms_per_image": direct_ms_img, "ms_per_image_selfconv": tc_ms_img,
                             "speedup": direct_ms_img / tc_ms_img},
         "single_image_latency_ms": {"min": min(lat), "median": statistics.median(lat)},

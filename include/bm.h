@@ -208,6 +208,44 @@ int bm_set_timing(bm_ctx* ctx, int enable);
 int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset);
 
 /*
+ * Patch groups (§IV, the group matrix after Eq. equ:self-convMM):
+ * Y_r = [y_S(1), ..., y_S(K)], the K matched patches of reference r, as
+ *   out_groups[r][k][(u*patch + v)*C + c] = img[y + u][x + v][c]
+ * where idx[r][k] = y*W + x (the layout bm_match writes: r = ry*n_rx + rx
+ * over the n_ry x n_rx reference grid).  An index that is not a top-left
+ * of the candidate grid (-1, or out of range) gives a zero patch.
+ * img: device, H x W x C, uint8 or float32 (dtype); idx: device int32
+ * [n_ry*n_rx][K]; out_groups: device, same element type as img,
+ * [n_ry*n_rx][K][patch*patch*C], caller-owned.  Asynchronous on `stream`.
+ * Validation: 1 <= C <= 8, 1 <= patch <= min(H, W), n_ry, n_rx >= 0,
+ * 1 <= K <= 128, non-null pointers (BM_ERR_INVALID, nothing launched);
+ * H*W < 2^31 (BM_ERR_UNSUPPORTED).  An empty grid launches nothing.
+ */
+int bm_gather_groups(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
+                     int patch, const int32_t* idx, int n_ry, int n_rx, int K,
+                     void* out_groups, bm_stream stream);
+
+/*
+ * Image reconstruction (§IV, "Image Reconstruction"): every patch
+ * groups[r][k] (layout of bm_gather_groups, float32) is deposited back at
+ * idx[r][k] and every pixel is divided by the number of deposited patches
+ * that contain it; with weights (nullable, float32 [n_ry*n_rx][K]) by their
+ * sum instead:
+ *   out_img[y][x][c] = sum w * Z / sum w,   out_weight[y][x] = sum w,
+ * both over the patches covering (y, x); 0 where no patch covers the pixel
+ * (or the weights sum to 0).  Patches whose index is not a top-left of the
+ * candidate grid are skipped.  out_img (H x W x C) and out_weight (H x W)
+ * are device float32 buffers owned by the caller; both are overwritten.
+ * The sums are accumulated in float32 in an unspecified order (atomics):
+ * each pixel is within (n + 1) * 2^-23 * sum |w Z| / |sum w| of the exact
+ * value, n the number of covering patches; unweighted counts are exact.
+ * Same validation as bm_gather_groups (out_img and out_weight required).
+ */
+int bm_aggregate(bm_ctx* ctx, const float* groups, const int32_t* idx, const float* weights,
+                 int n_ry, int n_rx, int K, int H, int W, int C, int patch,
+                 float* out_img, float* out_weight, bm_stream stream);
+
+/*
  * bm_match_static -- bm_match without any allocation.
  *
  * The paper has no counterpart: this entry point serves callers that must

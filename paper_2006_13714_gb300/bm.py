@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
             "bm_get_timing": ([vp, ctypes.POINTER(bm_timing), ci], ci),
             "bm_static_scratch_bytes": ([ci, ci, ci, ci, ci, ci, ci, ci], sz),
             "bm_match_static": ([vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
+            "bm_gather_groups": ([vp, vp, ci, ci, ci, ci, ci, vp, ci, ci, ci, vp, vp], ci),
+            "bm_aggregate": ([vp, vp, vp, vp, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -145,6 +147,18 @@ def bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx, out_
     """No-allocation matcher (fixed device scratch shared by all calls; see bm.h)."""
     return load().bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx,
                                   out_dist, stream)
+
+
+def bm_gather_groups(ctx, img, H, W, C, dtype, patch, idx, n_ry, n_rx, K, out_groups,
+                     stream) -> int:
+    return load().bm_gather_groups(ctx, img, H, W, C, dtype, patch, idx, n_ry, n_rx, K,
+                                   out_groups, stream)
+
+
+def bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch, out_img, out_weight,
+                 stream) -> int:
+    return load().bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch,
+                               out_img, out_weight, stream)
 
 
 def bm_match_host(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist) -> int:
@@ -312,6 +326,39 @@ class Context:
         rc, done, status = bm_poll(self.handle, ticket)
         self._check(rc)
         return bool(done), status
+
+    def gather_groups(self, img, patch, idx, n_ry, n_rx, out=None, stream=None):
+        """Patch groups [n_ry*n_rx, K, patch*patch*C] (img's dtype) of the matches idx."""
+        import torch
+        if not img.is_cuda or not img.is_contiguous() or not idx.is_contiguous():
+            raise ValueError("image and idx must be contiguous CUDA tensors")
+        H, W, C = _hwc(img)
+        K = idx.shape[-1]
+        if out is None:
+            out = torch.empty((n_ry * n_rx, K, patch * patch * C), dtype=img.dtype,
+                              device=img.device)
+        st = stream if stream is not None else torch.cuda.current_stream(img.device)
+        self._check(bm_gather_groups(self.handle, img.data_ptr(), H, W, C, _dtype_code(img), patch,
+                                     idx.data_ptr(), n_ry, n_rx, K, out.data_ptr(),
+                                     st.cuda_stream))
+        return out
+
+    def aggregate(self, groups, idx, H, W, C, patch, n_ry, n_rx, weights=None, out=None,
+                  stream=None):
+        """Reconstruction: (image [H, W, C] float32, weight map [H, W] float32)."""
+        import torch
+        if groups.dtype != torch.float32 or not groups.is_contiguous() or not idx.is_contiguous():
+            raise ValueError("groups must be contiguous float32, idx contiguous int32")
+        K = idx.shape[-1]
+        if out is None:
+            out = (torch.empty((H, W, C), dtype=torch.float32, device=groups.device),
+                   torch.empty((H, W), dtype=torch.float32, device=groups.device))
+        st = stream if stream is not None else torch.cuda.current_stream(groups.device)
+        wp = weights.data_ptr() if weights is not None else None
+        self._check(bm_aggregate(self.handle, groups.data_ptr(), idx.data_ptr(), wp, n_ry, n_rx,
+                                 K, H, W, C, patch, out[0].data_ptr(), out[1].data_ptr(),
+                                 st.cuda_stream))
+        return out
 
     def stats(self) -> dict:
         return bm_get_stats(self.handle)

@@ -510,6 +510,14 @@ int get_stream_ws(bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out) {
     return BM_OK;
 }
 
+}  // namespace
+
+namespace bm {
+int ctx_device(const ::bm_ctx* ctx) { return ctx->device; }
+}  // namespace bm
+
+namespace {
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {

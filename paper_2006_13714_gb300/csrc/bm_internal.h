@@ -10,7 +10,12 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct bm_ctx;
+
 namespace bm {
+
+// Device ordinal of a context (bm_api.cu).
+int ctx_device(const ::bm_ctx* ctx);
 
 constexpr int kMaxK = 128;        // largest K served
 constexpr int kMaxPatchElems = 256;  // p*p*C limit of every kernel
@@ -138,5 +143,17 @@ cudaError_t launch_rerank_batch(const Geom* gs, const RerankArgs* as, int n,
 
 // Sets the calling thread's bm_last_error message and returns code.
 int set_error(int code, const char* msg);
+
+// (f1) patch groups and reconstruction (groups.cu).
+// groups[pt][u][v*C + c] = img[y + u][x + v][c] for idx[pt] = y*W + x (pt =
+// r*K + k); a patch whose index is not a top-left of the candidate grid is 0.
+cudaError_t launch_gather_groups(const void* img, int dtype, const int32_t* idx, void* out,
+                                 long long n_patches, int H, int W, int C, int p,
+                                 cudaStream_t st);
+// out = sum w Z / sum w over the patches deposited at idx (wsum receives the
+// per-pixel sum of weights; 0 where none): zeroes both, accumulates, divides.
+cudaError_t launch_aggregate(const float* groups, const int32_t* idx, const float* weights,
+                             int n_ry, int n_rx, int K, int H, int W, int C, int p, float* out,
+                             float* wsum, cudaStream_t st);
 
 }  // namespace bm
