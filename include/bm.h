@@ -219,7 +219,8 @@ int bm_get_timing(bm_ctx* ctx, bm_timing* out, int reset);
  * [n_ry*n_rx][K][patch*patch*C], caller-owned.  Asynchronous on `stream`.
  * Validation: 1 <= C <= 8, 1 <= patch <= min(H, W), n_ry, n_rx >= 0,
  * 1 <= K <= 128, non-null pointers (BM_ERR_INVALID, nothing launched);
- * H*W < 2^31 (BM_ERR_UNSUPPORTED).  An empty grid launches nothing.
+ * H*W < 2^31 and patch*patch*C <= 256 (BM_ERR_UNSUPPORTED).  An empty
+ * grid launches nothing.
  */
 int bm_gather_groups(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype,
                      int patch, const int32_t* idx, int n_ry, int n_rx, int K,

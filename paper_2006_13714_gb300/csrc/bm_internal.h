@@ -14,6 +14,30 @@ struct bm_ctx;
 
 namespace bm {
 
+// n / d for every n in [0, 2^31) by a multiply-high and two shifts (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994;
+// the round-up method): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n).
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l > 0 ? 1 : 0;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
+    const unsigned t = __umulhi((unsigned)n, f.m);
+    return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
+}
+
 // Device ordinal of a context (bm_api.cu).
 int ctx_device(const ::bm_ctx* ctx);
 
@@ -148,7 +172,7 @@ int set_error(int code, const char* msg);
 // groups[pt][u][v*C + c] = img[y + u][x + v][c] for idx[pt] = y*W + x (pt =
 // r*K + k); a patch whose index is not a top-left of the candidate grid is 0.
 cudaError_t launch_gather_groups(const void* img, int dtype, const int32_t* idx, void* out,
-                                 long long n_patches, int H, int W, int C, int p,
+                                 int n_ry, int n_rx, int K, int H, int W, int C, int p,
                                  cudaStream_t st);
 // out = sum w Z / sum w over the patches deposited at idx (wsum receives the
 // per-pixel sum of weights; 0 where none): zeroes both, accumulates, divides.

@@ -57,30 +57,6 @@ constexpr int kCandCap = kFbSlots * 32;  // window keys kept per overflow refere
 constexpr int kMaxRerankJobs = 64;
 constexpr int kTileSmemLimit = 160 * 1024;
 
-// n / d for every 32-bit n by a multiply-high and two shifts (Granlund and
-// Montgomery, "Division by invariant integers using multiplication", 1994;
-// the round-up method): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
-// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n).
-struct FastDiv {
-    unsigned m;
-    int s1, s2;
-};
-
-FastDiv make_fastdiv(unsigned d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;
-    FastDiv f;
-    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
-    f.s1 = l > 0 ? 1 : 0;
-    f.s2 = l > 0 ? l - 1 : 0;
-    return f;
-}
-
-__device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
-    const unsigned t = __umulhi((unsigned)n, f.m);
-    return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
-}
-
 struct RerankJob {
     const float* img;
     const float* nrm;

@@ -135,6 +135,9 @@ def test_gather_unaligned_output_buffer(ctx):
 AGG = [
     # name,        H,   W,  C, p, win, s,  K, weighted
     ("a_p8",       90,  77, 1, 8, 39, 3, 16, False),
+    ("a_p8_w4",    96,  88, 1, 8, 39, 3, 16, False),   # W % 4 == 0: quad reductions
+    ("a_c4_w4",    64,  52, 4, 8, 15, 3, 32, True),
+    ("a_p5_w4",    48,  44, 1, 5, 11, 2, 12, True),
     ("a_p8_w",     90,  77, 1, 8, 39, 3, 16, True),
     ("a_c4",       60,  50, 4, 8, 15, 3, 32, False),
     ("a_p7_w",     70,  66, 1, 7, 21, 4, 20, True),
@@ -154,9 +157,9 @@ def test_aggregate_within_bound(ctx, case):
     check_aggregate(ctx, Z, idx, H, W, C, p, ny, nx, weights=w)
 
 
-def test_aggregate_scattered_indices_take_the_global_path(ctx):
-    # indices spread over the whole image: the tiles' bounding boxes exceed
-    # the shared-memory accumulator, so blocks deposit straight to the output
+def test_aggregate_scattered_indices(ctx):
+    # indices spread over the whole image, four channels: many patches of
+    # different references overlap at random
     H, W, C, p = 300, 280, 4, 8
     rng = np.random.default_rng(9)
     ny, nx, K = 12, 10, 24
@@ -200,3 +203,7 @@ def test_empty_grid_and_invalid_arguments(ctx):
     rc = B.bm_aggregate(h, img.data_ptr(), idx.data_ptr(), None, 1, 1, 4, 16, 16, 1, 4,
                         img.data_ptr(), None, None)
     assert rc == B.BM_ERR_INVALID
+    # patch volume beyond 256 elements (9 * 9 * 4): unsupported, as for bm_match
+    rc = B.bm_aggregate(h, img.data_ptr(), idx.data_ptr(), None, 1, 1, 4, 16, 16, 4, 9,
+                        img.data_ptr(), img.data_ptr(), None)
+    assert rc == B.BM_ERR_UNSUPPORTED
