@@ -349,6 +349,41 @@ def groups_throughput(ctx, imgs, outs, peaks, stream, dev, n=16):
             "groups_per_image": ny * nx, "layout": "float32 [refs][K][p*p]"}
 
 
+NLM_B = 283.0  # b of Eq. equ:nlm for the 512^2, sigma 25, 8x8 workload: d / b^2 ~ 1 for similar patches
+
+
+def nlm_throughput(ctx, imgs, stream, dev, pairs, n=16):
+    """Non-local means (Eq. equ:nlm) on n images of the workload: full-window
+    weights and patch estimates, CUDA events on the launch stream.  Roofline:
+    ALU (FP32), 4 p^2 C FLOP per (reference, candidate) pair against the
+    nominal FP32 FMA rate of 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz."""
+    import torch
+    H, W, p, win, s = WL["H"], WL["W"], WL["patch"], WL["window"], WL["stride"]
+    ny, nx = (H - p) // s + 1, (W - p) // s + 1
+    n = min(n, len(imgs))
+    outs = [(torch.empty((ny * nx, p * p), dtype=torch.float32, device=dev),
+             torch.empty((ny * nx,), dtype=torch.float32, device=dev)) for _ in range(n)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for rep in range(3):  # 1 warm-up + 2 timed
+        e0.record(stream)
+        for i in range(n):
+            ctx.nlm(imgs[i], p, win, s, NLM_B, out=outs[i], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rep:
+            times.append(e0.elapsed_time(e1) / n)
+    ms = min(times)
+    flop = 4.0 * pairs * p * p
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = flop / (ms / 1e3) / 1e12
+    return {"images": n, "us_per_image": 1e3 * ms, "ref_patches_per_s": ny * nx / (ms / 1e3),
+            "b": NLM_B, "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                    "unit": "TFLOP/s", "frac": achieved / peak,
+                                    "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz)",
+                                    "algorithmic_flop_per_image": flop}}
+
+
 def run_ours(args, world, rank, local, dist):
     import torch
     import paper_2006_13714_gb300 as pkg
@@ -486,6 +521,7 @@ def run_ours(args, world, rank, local, dist):
 
     serve = serve_latency(ctx, pkg, synth, dev) if not args.no_serve else None
     groups = groups_throughput(ctx, imgs, outs, peaks, stream, dev)
+    nlm = nlm_throughput(ctx, imgs, stream, dev, pairs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -519,6 +555,7 @@ def run_ours(args, world, rank, local, dist):
         "kernel_ms_per_step_with_stage_events": staged_ms,
         "serve": serve,
         "groups": groups,
+        "nlm": nlm,
         "direct_fp32_gpu": {"ms_per_image": direct_ms_img, "ms_per_image_selfconv": tc_ms_img,
                             "speedup": direct_ms_img / tc_ms_img},
         "single_image_latency_ms": {"min": min(lat), "median": statistics.median(lat)},

@@ -247,6 +247,25 @@ int bm_aggregate(bm_ctx* ctx, const float* groups, const int32_t* idx, const flo
                  float* out_img, float* out_weight, bm_stream stream);
 
 /*
+ * Non-local means (§III-A, Eq. equ:nlm; Prop. 1 gives the same weights
+ * through Self-Convolution), over the same clipped search windows and
+ * reference grid as bm_match.  For every reference r (row-major over the
+ * n_ry x n_rx grid) and every candidate j of its window:
+ *   w_r(j) = exp(-||X_j - X_r||_F^2 / b^2),  Theta_r = sum_j w_r(j),
+ *   out_est[r][(u*patch + v)*C + c] = sum_j w_r(j) X_j[u][v][c] / Theta_r,
+ *   out_theta[r] = Theta_r   (nullable; >= 1, the reference is a candidate).
+ * img: device, H x W x C, uint8 or float32; out_est / out_theta: device
+ * float32, caller-owned.  Computed in float32 (distances directly, packed
+ * FP32); each estimate is within about 2^-17 of the data range of the
+ * exact value.  Asynchronous on `stream`.
+ * Validation: geometry as bm_match, b > 0 and finite, non-null img and
+ * out_est (BM_ERR_INVALID, nothing launched); patch*patch*C <= 64 and a
+ * search region that fits in shared memory (BM_ERR_UNSUPPORTED).
+ */
+int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+           int window, int stride, float b, float* out_est, float* out_theta, bm_stream stream);
+
+/*
  * bm_match_static -- bm_match without any allocation.
  *
  * The paper has no counterpart: this entry point serves callers that must
