@@ -247,6 +247,25 @@ int bm_aggregate(bm_ctx* ctx, const float* groups, const int32_t* idx, const flo
                  float* out_img, float* out_weight, bm_stream stream);
 
 /*
+ * Block matching by normalized cross-correlation (§III-A, Eq. equ:cor;
+ * Lemma 1 and Theorem 1, case 3): over the same clipped search windows and
+ * reference grid as bm_match, the K candidates with the largest
+ *   ncc(r, j) = <X_r, X_j> / (||X_r||_F ||X_j||_F)
+ * (the uncentred cosine; a patch of zero norm scores 0), ties broken by the
+ * smaller row-major offset.  out_idx int32 [n_ry*n_rx][K] (offsets y*W + x,
+ * best first, -1 padding), out_score float32 (-inf padding).  uint8: the
+ * ranking is exact (integer cross terms and norms compared in 128-bit
+ * integers) and the scores are the correctly rounded quotient of exact
+ * integers; float32: ranked by the float32 score, within 2e-5 of the exact
+ * cosine.  Device pointers, asynchronous on `stream`.  Validation as
+ * bm_match (BM_ERR_INVALID / BM_ERR_UNSUPPORTED); additionally K <= 64 and a
+ * search region that fits in shared memory (BM_ERR_UNSUPPORTED).
+ */
+int bm_match_ncc(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                 int window, int stride, int K, int32_t* out_idx, float* out_score,
+                 bm_stream stream);
+
+/*
  * Non-local means (§III-A, Eq. equ:nlm; Prop. 1 gives the same weights
  * through Self-Convolution), over the same clipped search windows and
  * reference grid as bm_match.  For every reference r (row-major over the

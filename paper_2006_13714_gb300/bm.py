@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
             "bm_gather_groups": ([vp, vp, ci, ci, ci, ci, ci, vp, ci, ci, ci, vp, vp], ci),
             "bm_aggregate": ([vp, vp, vp, vp, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_nlm": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ctypes.c_float, vp, vp, vp], ci),
+            "bm_match_ncc": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -160,6 +161,12 @@ def bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch, out_i
                  stream) -> int:
     return load().bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch,
                                out_img, out_weight, stream)
+
+
+def bm_match_ncc(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_score,
+                 stream) -> int:
+    return load().bm_match_ncc(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx,
+                               out_score, stream)
 
 
 def bm_nlm(ctx, img, H, W, C, dtype, patch, window, stride, b, out_est, out_theta, stream) -> int:
@@ -363,6 +370,22 @@ class Context:
         wp = weights.data_ptr() if weights is not None else None
         self._check(bm_aggregate(self.handle, groups.data_ptr(), idx.data_ptr(), wp, n_ry, n_rx,
                                  K, H, W, C, patch, out[0].data_ptr(), out[1].data_ptr(),
+                                 st.cuda_stream))
+        return out
+
+    def match_ncc(self, img, patch, window, stride, K, out=None, stream=None):
+        """NCC block matching: (idx int32 [nR, K], score float32 [nR, K]), best first."""
+        import torch
+        if not img.is_cuda or not img.is_contiguous():
+            raise ValueError("image must be a contiguous CUDA tensor")
+        H, W, C = _hwc(img)
+        ry, rx = bm_num_refs(H, W, patch, stride)
+        if out is None:
+            out = (torch.empty((ry * rx, K), dtype=torch.int32, device=img.device),
+                   torch.empty((ry * rx, K), dtype=torch.float32, device=img.device))
+        st = stream if stream is not None else torch.cuda.current_stream(img.device)
+        self._check(bm_match_ncc(self.handle, img.data_ptr(), H, W, C, _dtype_code(img), patch,
+                                 window, stride, K, out[0].data_ptr(), out[1].data_ptr(),
                                  st.cuda_stream))
         return out
 

@@ -1,0 +1,231 @@
+// ncc.cu -- block matching by normalized cross-correlation (§III-A,
+// Eq. equ:cor; Lemma 1 and Theorem 1, case 3: the same ranking is the
+// Self-Convolution cross term C_r(j) scaled by g(j) = 1 / (||X_r|| ||X_j||)).
+//
+// For every reference X_r of the stride grid, the K candidates of its clipped
+// search window with the largest
+//   ncc(r, j) = <X_r, X_j> / (||X_r||_F ||X_j||_F)
+// (the uncentred cosine; a patch of zero norm scores 0), ties broken by the
+// smaller row-major offset.  uint8: the cross term a_j and the norm n_j are
+// exact integers (float32 sums of integers below 2^24), and a_j / sqrt(n_j)
+// is ranked exactly through a_j^2 n_k versus a_k^2 n_j in 128-bit integers,
+// so indices are exact.  float32: ranked by the float32 score.
+//
+// GB300 layout of the work (CUDA cores).  One block per 8 x 8 tile of
+// references, one thread per reference; the union of the tile's windows is
+// staged in shared memory (float32); each thread keeps its K best candidates
+// in a max-heap (worst at the root) in shared memory.
+#include "bm.h"
+#include "bm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+namespace bm {
+namespace {
+
+constexpr int kNccTile = 8;
+constexpr int kNccThreads = kNccTile * kNccTile;
+constexpr int kNccMaxK = 64;
+constexpr int kNccSmemLimit = 200 * 1024;
+
+struct NccParams {
+    const void* img;
+    int32_t* out_idx;  // [n_ry*n_rx][K]
+    float* out_score;  // [n_ry*n_rx][K]
+    int H, W, C, p, h, s, K, n_ry, n_rx, Hc, Wc, tiles_x;
+    int dtype;
+};
+
+// Heap entry: cross term and norm (uint8: exact integers; float32: the
+// score in `a`, `n` unused) and the candidate offset.
+struct Ent {
+    float a, n;
+    int off;
+};
+
+// true if x ranks before y (larger score, then smaller offset)
+template <bool kU8>
+__device__ __forceinline__ bool better(const Ent& x, const Ent& y) {
+    if (x.off < 0 || y.off < 0) return y.off < 0 && x.off >= 0;  // empty slots rank last
+    if (kU8) {
+        const unsigned long long ax = (unsigned long long)x.a, ay = (unsigned long long)y.a;
+        const unsigned long long A = ax * ax, B = ay * ay;
+        const unsigned long long nx = (unsigned long long)x.n, ny = (unsigned long long)y.n;
+        const unsigned long long h1 = __umul64hi(A, ny), l1 = A * ny;  // a_x^2 n_y
+        const unsigned long long h2 = __umul64hi(B, nx), l2 = B * nx;  // a_y^2 n_x
+        if (h1 != h2) return h1 > h2;
+        if (l1 != l2) return l1 > l2;
+    } else {
+        if (x.a != y.a) return x.a > y.a;
+    }
+    return x.off < y.off;
+}
+
+// Max-heap of the K best (worst at the root), entry i of thread t at h[i * nthr].
+template <bool kU8>
+__device__ void heap_push(Ent* h, int nthr, int K, const Ent& e) {
+    if (!better<kU8>(e, h[0])) return;
+    int i = 0;
+    while (true) {
+        const int l = 2 * i + 1;
+        if (l >= K) break;
+        int c = l;
+        if (l + 1 < K && better<kU8>(h[l * nthr], h[(l + 1) * nthr])) c = l + 1;  // worse child
+        if (!better<kU8>(e, h[c * nthr])) break;  // e is worse than (or as bad as) the worse child: stop
+        h[i * nthr] = h[c * nthr];
+        i = c;
+    }
+    h[i * nthr] = e;
+}
+
+template <bool kU8>
+__global__ void __launch_bounds__(kNccThreads) ncc_kernel(const NccParams Q) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int ty = blockIdx.x / Q.tiles_x, tx = blockIdx.x - ty * Q.tiles_x;
+    const int ry0 = ty * kNccTile, rx0 = tx * kNccTile;
+    const int ry1 = min(ry0 + kNccTile, Q.n_ry) - 1, rx1 = min(rx0 + kNccTile, Q.n_rx) - 1;
+    const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
+    const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + Q.p, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + Q.p;
+    const int nrow = Y1 - Y0, pitch = (X1 - X0) * Q.C;
+    float* sreg = reinterpret_cast<float*>(smem);
+    Ent* heap = reinterpret_cast<Ent*>(smem + (((size_t)nrow * pitch * 4 + 15) & ~size_t(15)));
+    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
+        const int r = i / pitch, e = i - r * pitch;
+        const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * Q.C + e;
+        sreg[i] = kU8 ? (float)static_cast<const uint8_t*>(Q.img)[g] : static_cast<const float*>(Q.img)[g];
+    }
+    Ent* h = heap + threadIdx.x;
+    for (int i = 0; i < Q.K; ++i) h[i * kNccThreads] = Ent{0.f, 1.f, -1};
+    __syncthreads();
+    const int ry = ry0 + threadIdx.x / kNccTile, rx = rx0 + threadIdx.x % kNccTile;
+    if (ry > ry1 || rx > rx1) return;
+    const int yr = ry * Q.s, xr = rx * Q.s, pc = Q.p * Q.C;
+    const float* rp = sreg + (yr - Y0) * pitch + (xr - X0) * Q.C;
+    float nr = 0.f;
+    for (int u = 0; u < Q.p; ++u)
+        for (int e = 0; e < pc; ++e) nr = fmaf(rp[u * pitch + e], rp[u * pitch + e], nr);
+    const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
+    const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
+    for (int yc = cy0; yc <= cy1; ++yc) {
+        for (int xc = cx0; xc <= cx1; ++xc) {
+            const float* cp = sreg + (yc - Y0) * pitch + (xc - X0) * Q.C;
+            float a = 0.f, n = 0.f;
+            for (int u = 0; u < Q.p; ++u) {
+                const float* cr = cp + u * pitch;
+                const float* rr = rp + u * pitch;
+#pragma unroll 8
+                for (int e = 0; e < pc; ++e) {
+                    const float c = cr[e];
+                    a = fmaf(rr[e], c, a);
+                    n = fmaf(c, c, n);
+                }
+            }
+            Ent ent;
+            ent.off = yc * Q.W + xc;
+            if (kU8) {
+                // zero norms score 0
+                const bool z = n == 0.f || nr == 0.f;
+                ent.a = z ? 0.f : a;
+                ent.n = z ? 1.f : n;
+            } else {
+                ent.a = (n > 0.f && nr > 0.f) ? a * rsqrtf(n) : 0.f;
+                ent.n = 1.f;
+            }
+            heap_push<kU8>(h, kNccThreads, Q.K, ent);
+        }
+    }
+    // heap sort: repeatedly move the root (worst) to the end
+    for (int m = Q.K - 1; m > 0; --m) {
+        const Ent top = h[0];
+        const Ent last = h[m * kNccThreads];
+        h[m * kNccThreads] = top;
+        // sift `last` down in h[0 .. m)
+        int i = 0;
+        while (true) {
+            const int l = 2 * i + 1;
+            if (l >= m) break;
+            int c = l;
+            if (l + 1 < m && better<kU8>(h[l * kNccThreads], h[(l + 1) * kNccThreads])) c = l + 1;
+            if (!better<kU8>(last, h[c * kNccThreads])) break;
+            h[i * kNccThreads] = h[c * kNccThreads];
+            i = c;
+        }
+        h[i * kNccThreads] = last;
+    }
+    // h[0] is now the best, h[K-1] the worst
+    const size_t ref = (size_t)ry * Q.n_rx + rx;
+    const float inr = nr > 0.f ? rsqrtf(nr) : 0.f;
+    for (int k = 0; k < Q.K; ++k) {
+        const Ent e = h[k * kNccThreads];
+        Q.out_idx[ref * Q.K + k] = e.off;
+        float sc = -__int_as_float(0x7f800000);
+        if (e.off >= 0) {
+            if (kU8) sc = nr > 0.f ? (float)((double)e.a / sqrt((double)nr * (double)e.n)) : 0.f;
+            else sc = e.a * inr;
+        }
+        Q.out_score[ref * Q.K + k] = sc;
+    }
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" {
+
+int bm_match_ncc(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                 int window, int stride, int K, int32_t* out_idx, float* out_score,
+                 bm_stream stream) {
+    if (!ctx) return set_error(BM_ERR_INVALID, "null context");
+    if (dtype != BM_U8 && dtype != BM_F32) return set_error(BM_ERR_INVALID, "unknown dtype");
+    if (H < 1 || W < 1 || C < 1 || C > kMaxC || patch < 1 || patch > H || patch > W ||
+        window < 1 || window % 2 == 0 || window > kMaxWindow || stride < 1 || K < 1 || K > kMaxK)
+        return set_error(BM_ERR_INVALID, "invalid geometry or K");
+    if (!img || !out_idx || !out_score) return set_error(BM_ERR_INVALID, "null pointer");
+    if ((long long)H * W >= (1LL << 31)) return set_error(BM_ERR_UNSUPPORTED, "H*W must be below 2^31");
+    if (patch * patch * C > kMaxPatchElems)
+        return set_error(BM_ERR_UNSUPPORTED, "patch*patch*C must be at most 256");
+    if (K > kNccMaxK) return set_error(BM_ERR_UNSUPPORTED, "K must be at most 64 for NCC");
+    NccParams Q{};
+    Q.img = img; Q.out_idx = out_idx; Q.out_score = out_score;
+    Q.H = H; Q.W = W; Q.C = C; Q.p = patch; Q.h = (window - 1) / 2; Q.s = stride; Q.K = K;
+    Q.n_ry = (H - patch) / stride + 1; Q.n_rx = (W - patch) / stride + 1;
+    Q.Hc = H - patch + 1; Q.Wc = W - patch + 1;
+    Q.dtype = dtype == BM_U8 ? kU8 : kF32;
+    Q.tiles_x = (Q.n_rx + kNccTile - 1) / kNccTile;
+    const int tiles = ((Q.n_ry + kNccTile - 1) / kNccTile) * Q.tiles_x;
+    const int rows = std::min(H, (kNccTile - 1) * stride + 2 * Q.h + patch);
+    const int cols = std::min(W, (kNccTile - 1) * stride + 2 * Q.h + patch);
+    const size_t smem = (((size_t)rows * cols * C * 4 + 15) & ~size_t(15)) +
+                        (size_t)K * kNccThreads * sizeof(Ent);
+    if (smem > (size_t)kNccSmemLimit)
+        return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");
+    DevGuard dg(ctx_device(ctx));
+    void (*kern)(NccParams) = Q.dtype == kU8 ? ncc_kernel<true> : ncc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        kern<<<tiles, kNccThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(Q);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return set_error(BM_ERR_CUDA, (std::string("ncc launch: ") + cudaGetErrorString(e)).c_str());
+    return BM_OK;
+}
+
+}  // extern "C"
