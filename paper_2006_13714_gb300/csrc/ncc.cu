@@ -12,9 +12,17 @@
 // so indices are exact.  float32: ranked by the float32 score.
 //
 // GB300 layout of the work (CUDA cores).  One block per 8 x 8 tile of
-// references, one thread per reference; the union of the tile's windows is
-// staged in shared memory (float32); each thread keeps its K best candidates
-// in a max-heap (worst at the root) in shared memory.
+// references; the union of the tile's windows is staged in shared memory.
+//   Fast path (K <= 32, instantiated patch shapes with p*p*C <= 64): the
+//   region is stored as element pairs (pair e of a row holds elements e and
+//   e + 1) and read with 64-bit loads; one warp per reference, one lane per
+//   candidate, cross term and norm two elements at a time with packed FP32
+//   (fma.rn.f32x2).  The warp keeps the K best candidates one per lane, in
+//   order; a round of 32 new candidates costs one ballot against the K-th,
+//   and each candidate that beats it is inserted at its rank (ballot count)
+//   with one shuffle of the list.
+//   General path: one thread per reference, its K best in a max-heap (worst
+//   at the root) in shared memory.
 #include "bm.h"
 #include "bm_internal.h"
 
@@ -169,6 +177,147 @@ __global__ void __launch_bounds__(kNccThreads) ncc_kernel(const NccParams Q) {
     }
 }
 
+// ---------------------------------------------------------------- fast path
+
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float sum2(unsigned long long v) {
+    return __uint_as_float((unsigned)v) + __uint_as_float((unsigned)(v >> 32));
+}
+
+template <int P, int C, bool kU8>
+__global__ void __launch_bounds__(256) ncc_warp_kernel(const NccParams Q) {
+    constexpr int PC = P * C, NPR = PC / 2, TAIL = PC & 1;
+    extern __shared__ __align__(16) float2 sp[];
+    const int ty = blockIdx.x / Q.tiles_x, tx = blockIdx.x - ty * Q.tiles_x;
+    const int ry0 = ty * kNccTile, rx0 = tx * kNccTile;
+    const int ry1 = min(ry0 + kNccTile, Q.n_ry) - 1, rx1 = min(rx0 + kNccTile, Q.n_rx) - 1;
+    const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
+    const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + P, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + P;
+    const int nrow = Y1 - Y0, pitch = (X1 - X0) * C;
+    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
+        const int r = i / pitch, e = i - r * pitch;
+        const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
+        float a, b;
+        if (kU8) {
+            const uint8_t* im = static_cast<const uint8_t*>(Q.img);
+            a = im[g];
+            b = e + 1 < pitch ? im[g + 1] : 0.f;
+        } else {
+            const float* im = static_cast<const float*>(Q.img);
+            a = im[g];
+            b = e + 1 < pitch ? im[g + 1] : 0.f;
+        }
+        sp[i] = make_float2(a, b);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int ntx = rx1 - rx0 + 1, nref = (ry1 - ry0 + 1) * ntx;
+    const int K = Q.K;
+    for (int rl = warp; rl < nref; rl += nwarps) {
+        const int ry = ry0 + rl / ntx, rx = rx0 + rl % ntx;
+        const int yr = ry * Q.s, xr = rx * Q.s;
+        const float2* rb = sp + (yr - Y0) * pitch + (xr - X0) * C;
+        unsigned long long nr2 = 0ull;
+        float nrt = 0.f;
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+#pragma unroll
+            for (int t = 0; t < NPR; ++t) {
+                const unsigned long long r2 = pk2(rb[u * pitch + 2 * t]);
+                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(nr2) : "l"(r2));
+            }
+            if (TAIL) nrt = fmaf(rb[u * pitch + PC - 1].x, rb[u * pitch + PC - 1].x, nrt);
+        }
+        const float nr = sum2(nr2) + nrt;
+        const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
+        const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
+        const int wx = cx1 - cx0 + 1, ncand = (cy1 - cy0 + 1) * wx;
+        // the list: entry `lane` (in rank order; lanes >= K hold nothing of use)
+        Ent mine{0.f, 1.f, -1};
+        Ent kth{0.f, 1.f, -1};
+        for (int j0 = 0; j0 < ncand; j0 += 32) {
+            const int j = j0 + lane;
+            Ent c{0.f, 1.f, -1};
+            if (j < ncand) {
+                const int jy = j / wx, jx = j - jy * wx;
+                const int yc = cy0 + jy, xc = cx0 + jx;
+                const float2* cb = sp + (yc - Y0) * pitch + (xc - X0) * C;
+                unsigned long long a2 = 0ull, n2 = 0ull;
+                float at = 0.f, nt = 0.f;
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+#pragma unroll
+                    for (int t = 0; t < NPR; ++t) {
+                        const unsigned long long c2 = pk2(cb[u * pitch + 2 * t]);
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(pk2(rb[u * pitch + 2 * t])), "l"(c2));
+                        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(n2) : "l"(c2));
+                    }
+                    if (TAIL) {
+                        const float cv = cb[u * pitch + PC - 1].x;
+                        at = fmaf(rb[u * pitch + PC - 1].x, cv, at);
+                        nt = fmaf(cv, cv, nt);
+                    }
+                }
+                const float a = sum2(a2) + at, n = sum2(n2) + nt;
+                c.off = yc * Q.W + xc;
+                if (kU8) {
+                    const bool z = n == 0.f || nr == 0.f;
+                    c.a = z ? 0.f : a;
+                    c.n = z ? 1.f : n;
+                } else {
+                    c.a = (n > 0.f && nr > 0.f) ? a * rsqrtf(n) : 0.f;
+                }
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, c.off >= 0 && better<kU8>(c, kth));
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                Ent b;
+                b.a = __shfl_sync(0xffffffffu, c.a, src);
+                b.n = __shfl_sync(0xffffffffu, c.n, src);
+                b.off = __shfl_sync(0xffffffffu, c.off, src);
+                if (!better<kU8>(b, kth)) continue;  // the K-th moved past it
+                const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && better<kU8>(mine, b)));
+                Ent up;
+                up.a = __shfl_up_sync(0xffffffffu, mine.a, 1);
+                up.n = __shfl_up_sync(0xffffffffu, mine.n, 1);
+                up.off = __shfl_up_sync(0xffffffffu, mine.off, 1);
+                if (lane == pos) mine = b;
+                else if (lane > pos) mine = up;
+                kth.a = __shfl_sync(0xffffffffu, mine.a, K - 1);
+                kth.n = __shfl_sync(0xffffffffu, mine.n, K - 1);
+                kth.off = __shfl_sync(0xffffffffu, mine.off, K - 1);
+            }
+        }
+        if (lane < K) {
+            const size_t ref = (size_t)ry * Q.n_rx + rx;
+            float sc = -__int_as_float(0x7f800000);
+            if (mine.off >= 0) {
+                if (kU8) sc = nr > 0.f ? (float)((double)mine.a / sqrt((double)nr * (double)mine.n)) : 0.f;
+                else sc = nr > 0.f ? mine.a * rsqrtf(nr) : 0.f;
+            }
+            Q.out_idx[ref * K + lane] = mine.off;
+            Q.out_score[ref * K + lane] = sc;
+        }
+    }
+}
+
+using NccKernel = void (*)(NccParams);
+
+NccKernel pick_fast(int p, int C, bool u8) {
+#define BM_NCC_CASE(PP, CC) \
+    if (p == PP && C == CC) return u8 ? ncc_warp_kernel<PP, CC, true> : ncc_warp_kernel<PP, CC, false>;
+    BM_NCC_CASE(1, 1) BM_NCC_CASE(2, 1) BM_NCC_CASE(3, 1) BM_NCC_CASE(4, 1) BM_NCC_CASE(5, 1)
+    BM_NCC_CASE(6, 1) BM_NCC_CASE(7, 1) BM_NCC_CASE(8, 1)
+    BM_NCC_CASE(2, 2) BM_NCC_CASE(3, 2) BM_NCC_CASE(4, 2)
+    BM_NCC_CASE(2, 3) BM_NCC_CASE(3, 3) BM_NCC_CASE(4, 3)
+    BM_NCC_CASE(2, 4) BM_NCC_CASE(3, 4) BM_NCC_CASE(4, 4)
+#undef BM_NCC_CASE
+    return nullptr;
+}
+
 struct DevGuard {
     int prev = -1;
     explicit DevGuard(int dev) {
@@ -212,15 +361,18 @@ int bm_match_ncc(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dty
     const int tiles = ((Q.n_ry + kNccTile - 1) / kNccTile) * Q.tiles_x;
     const int rows = std::min(H, (kNccTile - 1) * stride + 2 * Q.h + patch);
     const int cols = std::min(W, (kNccTile - 1) * stride + 2 * Q.h + patch);
-    const size_t smem = (((size_t)rows * cols * C * 4 + 15) & ~size_t(15)) +
-                        (size_t)K * kNccThreads * sizeof(Ent);
+    const size_t region = (size_t)rows * cols * C;
+    NccKernel fast = K <= 32 ? pick_fast(patch, C, Q.dtype == kU8) : nullptr;
+    if (fast && region * sizeof(float2) > (size_t)kNccSmemLimit) fast = nullptr;
+    const size_t smem = fast ? region * sizeof(float2)
+                             : ((region * 4 + 15) & ~size_t(15)) + (size_t)K * kNccThreads * sizeof(Ent);
     if (smem > (size_t)kNccSmemLimit)
         return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");
     DevGuard dg(ctx_device(ctx));
-    void (*kern)(NccParams) = Q.dtype == kU8 ? ncc_kernel<true> : ncc_kernel<false>;
+    NccKernel kern = fast ? fast : (Q.dtype == kU8 ? ncc_kernel<true> : ncc_kernel<false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        kern<<<tiles, kNccThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(Q);
+        kern<<<tiles, fast ? 256 : kNccThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(Q);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess)
