@@ -247,6 +247,26 @@ int bm_aggregate(bm_ctx* ctx, const float* groups, const int32_t* idx, const flo
                  float* out_img, float* out_weight, bm_stream stream);
 
 /*
+ * 3-D block matching across channels (§IV: the 3-D Self-Convolution on
+ * patches of depth d < C, searched across channels, the channel sum S(.)
+ * omitted).  A 3-D patch at (y, x, c) holds X[y + u][x + v][c + t] for
+ * u, v < patch, t < depth.  References: the spatial grid of bm_match at every
+ * channel offset c_r in [0, C - depth]; row index
+ * (ry * n_rx + rx) * (C - depth + 1) + c_r.  Candidates: the clipped spatial
+ * window of bm_match at every channel offset.  out_idx int32
+ * [n_ry*n_rx*(C-depth+1)][K]: offsets (y * W + x) * C + c (the flat HWC index
+ * of the candidate's first element), nearest first by (distance, offset),
+ * -1 padding; out_dist int32 (uint8, exact; INT32_MAX padding) or float32
+ * (float32 sums of squared differences; +inf padding).  Device pointers,
+ * asynchronous on `stream`.  Validation as bm_match plus 1 <= depth <= C
+ * (BM_ERR_INVALID); patch*patch*depth <= 128, K <= 32, H*W*C < 2^31 and a
+ * search region that fits in shared memory (BM_ERR_UNSUPPORTED).
+ */
+int bm_match_3d(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                int depth, int window, int stride, int K, int32_t* out_idx, void* out_dist,
+                bm_stream stream);
+
+/*
  * Block matching by normalized cross-correlation (§III-A, Eq. equ:cor;
  * Lemma 1 and Theorem 1, case 3): over the same clipped search windows and
  * reference grid as bm_match, the K candidates with the largest

@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
             "bm_aggregate": ([vp, vp, vp, vp, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_nlm": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ctypes.c_float, vp, vp, vp], ci),
             "bm_match_ncc": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
+            "bm_match_3d": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -161,6 +162,12 @@ def bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch, out_i
                  stream) -> int:
     return load().bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch,
                                out_img, out_weight, stream)
+
+
+def bm_match_3d(ctx, img, H, W, C, dtype, patch, depth, window, stride, K, out_idx, out_dist,
+                stream) -> int:
+    return load().bm_match_3d(ctx, img, H, W, C, dtype, patch, depth, window, stride, K, out_idx,
+                              out_dist, stream)
 
 
 def bm_match_ncc(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_score,
@@ -371,6 +378,24 @@ class Context:
         self._check(bm_aggregate(self.handle, groups.data_ptr(), idx.data_ptr(), wp, n_ry, n_rx,
                                  K, H, W, C, patch, out[0].data_ptr(), out[1].data_ptr(),
                                  st.cuda_stream))
+        return out
+
+    def match_3d(self, img, patch, depth, window, stride, K, out=None, stream=None):
+        """3-D block matching across channels: (idx [nR*(C-depth+1), K], dist), nearest first."""
+        import torch
+        if not img.is_cuda or not img.is_contiguous():
+            raise ValueError("image must be a contiguous CUDA tensor")
+        H, W, C = _hwc(img)
+        ry, rx = bm_num_refs(H, W, patch, stride)
+        n = ry * rx * (C - depth + 1)
+        if out is None:
+            out = (torch.empty((n, K), dtype=torch.int32, device=img.device),
+                   torch.empty((n, K), dtype=torch.int32 if img.dtype == torch.uint8
+                               else torch.float32, device=img.device))
+        st = stream if stream is not None else torch.cuda.current_stream(img.device)
+        self._check(bm_match_3d(self.handle, img.data_ptr(), H, W, C, _dtype_code(img), patch,
+                                depth, window, stride, K, out[0].data_ptr(), out[1].data_ptr(),
+                                st.cuda_stream))
         return out
 
     def match_ncc(self, img, patch, window, stride, K, out=None, stream=None):

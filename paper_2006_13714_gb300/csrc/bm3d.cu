@@ -1,0 +1,204 @@
+// bm3d.cu -- 3-D block matching across channels (§IV: 3-D Self-Convolution on
+// patches of depth d < C channels, searched across channels, the channel sum
+// S(.) omitted).
+//
+// A 3-D patch at (y, x, c) holds X[y + u][x + v][c + t], u, v < p, t < d.
+// References: the spatial stride grid of block matching at every channel
+// offset c_r in [0, C - d], reference index (ry * n_rx + rx) * (C - d + 1) + c_r.
+// Candidates: the clipped spatial search window of block matching at every
+// channel offset.  Output: the K nearest by (distance, offset), offset =
+// (y * W + x) * C + c (the flat HWC index of the patch's first element).
+// uint8 distances are exact (float32 sums of integers below 2^24); float32
+// distances are float32 sums of squared differences.
+//
+// GB300 layout of the work (CUDA cores).  One block per 8 x 8 tile of the
+// spatial reference grid; the union of the tile's windows (all channels) is
+// staged in shared memory.  One warp per (reference, channel offset), one lane
+// per candidate; the reference patch sits in registers.  The warp keeps its K
+// best (distance, offset) keys one per lane in rank order; a round of 32
+// candidates costs one ballot against the K-th, and each candidate that beats
+// it is inserted at its rank (ballot count) with one shuffle of the list.
+#include "bm.h"
+#include "bm_internal.h"
+
+#include <algorithm>
+#include <climits>
+#include <string>
+
+namespace bm {
+namespace {
+
+constexpr int kTile3 = 8;
+constexpr int kThreads3 = 256;
+constexpr int kMaxK3 = 32;
+constexpr int kMaxElems3 = 128;
+constexpr int kSmemLimit3 = 200 * 1024;
+constexpr unsigned long long kEmpty3 = ~0ull;
+
+struct Bm3dParams {
+    const void* img;
+    int32_t* out_idx;   // [n_ry*n_rx*nc][K]
+    void* out_dist;     // int32 (uint8) / float32 (float32)
+    int H, W, C, p, h, s, K, n_ry, n_rx, Hc, Wc, nc, tiles_x;
+};
+
+template <int P, int D, bool kU8>
+__global__ void __launch_bounds__(kThreads3) bm3d_kernel(const Bm3dParams Q) {
+    extern __shared__ __align__(16) float sreg[];
+    const int ty = blockIdx.x / Q.tiles_x, tx = blockIdx.x - ty * Q.tiles_x;
+    const int ry0 = ty * kTile3, rx0 = tx * kTile3;
+    const int ry1 = min(ry0 + kTile3, Q.n_ry) - 1, rx1 = min(rx0 + kTile3, Q.n_rx) - 1;
+    const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
+    const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + P, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + P;
+    const int C = Q.C, nrow = Y1 - Y0, pitch = (X1 - X0) * C;
+    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
+        const int r = i / pitch, e = i - r * pitch;
+        const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
+        sreg[i] = kU8 ? (float)static_cast<const uint8_t*>(Q.img)[g] : static_cast<const float*>(Q.img)[g];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int ntx = rx1 - rx0 + 1, nref = (ry1 - ry0 + 1) * ntx * Q.nc;
+    const int K = Q.K;
+    for (int rl = warp; rl < nref; rl += nwarps) {
+        const int rs = rl / Q.nc, cr = rl - rs * Q.nc;
+        const int ry = ry0 + rs / ntx, rx = rx0 + rs % ntx;
+        const int yr = ry * Q.s, xr = rx * Q.s;
+        float ref[P][P][D];
+#pragma unroll
+        for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int v = 0; v < P; ++v)
+#pragma unroll
+                for (int t = 0; t < D; ++t)
+                    ref[u][v][t] = sreg[(yr + u - Y0) * pitch + (xr + v - X0) * C + cr + t];
+        const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
+        const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
+        const int wx = cx1 - cx0 + 1, wxc = wx * Q.nc, ncand = (cy1 - cy0 + 1) * wxc;
+        unsigned long long mine = kEmpty3, kth = kEmpty3;
+        for (int j0 = 0; j0 < ncand; j0 += 32) {
+            const int j = j0 + lane;
+            unsigned long long key = kEmpty3;
+            if (j < ncand) {
+                const int jy = j / wxc, rem = j - jy * wxc;
+                const int jx = rem / Q.nc, cc = rem - jx * Q.nc;
+                const int yc = cy0 + jy, xc = cx0 + jx;
+                const float* cb = sreg + (yc - Y0) * pitch + (xc - X0) * C + cc;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int u = 0; u < P; ++u)
+#pragma unroll
+                    for (int v = 0; v < P; ++v)
+#pragma unroll
+                        for (int t = 0; t < D; ++t) {
+                            const float df = ref[u][v][t] - cb[u * pitch + v * C + t];
+                            if ((u * P + v) & 1) s1 = fmaf(df, df, s1);
+                            else s0 = fmaf(df, df, s0);
+                        }
+                const float d = s0 + s1;
+                const unsigned off = (unsigned)((yc * Q.W + xc) * C + cc);
+                key = kU8 ? ((unsigned long long)(unsigned)d << 32) | off
+                          : ((unsigned long long)__float_as_uint(d) << 32) | off;
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, key < kth);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const unsigned long long b = __shfl_sync(0xffffffffu, key, src);
+                if (!(b < kth)) continue;  // the K-th moved past it
+                const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && mine < b));
+                const unsigned long long up = __shfl_up_sync(0xffffffffu, mine, 1);
+                if (lane == pos) mine = b;
+                else if (lane > pos) mine = up;
+                kth = __shfl_sync(0xffffffffu, mine, K - 1);
+            }
+        }
+        if (lane < K) {
+            const size_t ref_id = ((size_t)ry * Q.n_rx + rx) * Q.nc + cr;
+            Q.out_idx[ref_id * K + lane] = mine == kEmpty3 ? -1 : (int32_t)(unsigned)mine;
+            if (kU8)
+                static_cast<int32_t*>(Q.out_dist)[ref_id * K + lane] =
+                    mine == kEmpty3 ? INT_MAX : (int32_t)(unsigned)(mine >> 32);
+            else
+                static_cast<float*>(Q.out_dist)[ref_id * K + lane] =
+                    mine == kEmpty3 ? __int_as_float(0x7f800000) : __uint_as_float((unsigned)(mine >> 32));
+        }
+    }
+}
+
+using Bm3dKernel = void (*)(Bm3dParams);
+
+Bm3dKernel pick3(int p, int d, bool u8) {
+#define BM3_CASE(PP, DD) \
+    if (p == PP && d == DD) return u8 ? bm3d_kernel<PP, DD, true> : bm3d_kernel<PP, DD, false>;
+    BM3_CASE(1, 1) BM3_CASE(2, 1) BM3_CASE(3, 1) BM3_CASE(4, 1) BM3_CASE(5, 1) BM3_CASE(6, 1)
+    BM3_CASE(7, 1) BM3_CASE(8, 1)
+    BM3_CASE(1, 2) BM3_CASE(2, 2) BM3_CASE(3, 2) BM3_CASE(4, 2) BM3_CASE(5, 2)
+    BM3_CASE(1, 3) BM3_CASE(2, 3) BM3_CASE(3, 3) BM3_CASE(4, 3)
+    BM3_CASE(2, 4) BM3_CASE(3, 4) BM3_CASE(4, 4)
+    BM3_CASE(6, 2) BM3_CASE(7, 2) BM3_CASE(8, 2) BM3_CASE(5, 3) BM3_CASE(6, 3) BM3_CASE(5, 4)
+#undef BM3_CASE
+    return nullptr;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" {
+
+int bm_match_3d(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, int patch,
+                int depth, int window, int stride, int K, int32_t* out_idx, void* out_dist,
+                bm_stream stream) {
+    if (!ctx) return set_error(BM_ERR_INVALID, "null context");
+    if (dtype != BM_U8 && dtype != BM_F32) return set_error(BM_ERR_INVALID, "unknown dtype");
+    if (H < 1 || W < 1 || C < 1 || C > kMaxC || patch < 1 || patch > H || patch > W ||
+        depth < 1 || depth > C || window < 1 || window % 2 == 0 || window > kMaxWindow ||
+        stride < 1 || K < 1 || K > kMaxK)
+        return set_error(BM_ERR_INVALID, "invalid geometry, depth or K");
+    if (!img || !out_idx || !out_dist) return set_error(BM_ERR_INVALID, "null pointer");
+    if ((long long)H * W * C >= (1LL << 31))
+        return set_error(BM_ERR_UNSUPPORTED, "H*W*C must be below 2^31");
+    if (patch * patch * depth > kMaxElems3 || K > kMaxK3)
+        return set_error(BM_ERR_UNSUPPORTED, "3-D matching serves patch*patch*depth <= 128 and K <= 32");
+    const bool u8 = dtype == BM_U8;
+    const Bm3dKernel kern = pick3(patch, depth, u8);
+    if (!kern) return set_error(BM_ERR_UNSUPPORTED, "patch / depth shape not instantiated");
+    Bm3dParams Q{};
+    Q.img = img; Q.out_idx = out_idx; Q.out_dist = out_dist;
+    Q.H = H; Q.W = W; Q.C = C; Q.p = patch; Q.h = (window - 1) / 2; Q.s = stride; Q.K = K;
+    Q.n_ry = (H - patch) / stride + 1; Q.n_rx = (W - patch) / stride + 1;
+    Q.Hc = H - patch + 1; Q.Wc = W - patch + 1; Q.nc = C - depth + 1;
+    Q.tiles_x = (Q.n_rx + kTile3 - 1) / kTile3;
+    const int tiles = ((Q.n_ry + kTile3 - 1) / kTile3) * Q.tiles_x;
+    const int rows = std::min(H, (kTile3 - 1) * stride + 2 * Q.h + patch);
+    const int cols = std::min(W, (kTile3 - 1) * stride + 2 * Q.h + patch);
+    const size_t smem = (size_t)rows * cols * C * sizeof(float);
+    if (smem > (size_t)kSmemLimit3)
+        return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");
+    DevGuard dg(ctx_device(ctx));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        kern<<<tiles, kThreads3, smem, reinterpret_cast<cudaStream_t>(stream)>>>(Q);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return set_error(BM_ERR_CUDA, (std::string("3-D match launch: ") + cudaGetErrorString(e)).c_str());
+    return BM_OK;
+}
+
+}  // extern "C"
