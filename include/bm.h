@@ -161,6 +161,26 @@ int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dt
  */
 int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream);
 
+/*
+ * Failure detection.  Every wait inside the tensor-core kernel is bounded
+ * (2 s); when one runs out, that CTA stops, waits for its copies and MMAs in
+ * flight, frees its tensor memory, and records the wait site in the
+ * context's sticky fault word (the outputs of that job are then invalid).
+ * bm_check synchronises `stream` and reports that word: BM_OK, or
+ * BM_ERR_TIMEOUT with the site in bm_last_error (the word is cleared, the
+ * context stays usable).  bm_match_host performs the same check before it
+ * returns.  Asynchronous entry points cannot report it themselves; call
+ * bm_check after the work of interest.
+ */
+int bm_check(bm_ctx* ctx, bm_stream stream);
+
+/*
+ * Test hook for the above: mode 1 makes the next tensor-core launch of
+ * bm_match (not bm_match_batch) withhold one stage publication in one CTA,
+ * so that a bounded wait runs out; mode 0 disarms it.  One-shot.
+ */
+int bm_set_fault_injection(bm_ctx* ctx, int mode);
+
 /* Select the algorithm used by bm_match / bm_match_batch / bm_submit. */
 int bm_set_algo(bm_ctx* ctx, bm_algo algo);
 

@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True):
             "bm_nlm": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ctypes.c_float, vp, vp, vp], ci),
             "bm_match_ncc": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_match_3d": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
+            "bm_check": ([vp, vp], ci),
+            "bm_set_fault_injection": ([vp, ci], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -162,6 +164,14 @@ def bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch, out_i
                  stream) -> int:
     return load().bm_aggregate(ctx, groups, idx, weights, n_ry, n_rx, K, H, W, C, patch,
                                out_img, out_weight, stream)
+
+
+def bm_check(ctx, stream) -> int:
+    return load().bm_check(ctx, stream)
+
+
+def bm_set_fault_injection(ctx, mode: int) -> int:
+    return load().bm_set_fault_injection(ctx, mode)
 
 
 def bm_match_3d(ctx, img, H, W, C, dtype, patch, depth, window, stride, K, out_idx, out_dist,

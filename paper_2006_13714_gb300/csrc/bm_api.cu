@@ -148,6 +148,8 @@ struct bm_ctx {
     std::unordered_map<cudaStream_t, Workspace> ws;  // per-stream cache
     std::mutex graph_mu;
     std::unordered_map<cudaStream_t, GraphEntry> graphs;  // captured batches, per stream
+    int* d_fault = nullptr;                          // sticky timeout word of the tensor-core kernel
+    std::atomic<int> inject{0};                      // one-shot fault injection (test hook)
     unsigned long long* d_counters = nullptr;        // [0] overflow, [1] fp64 rechecks
     std::atomic<unsigned long long> matches{0}, refs{0}, tc_jobs{0};
     // stage timing
@@ -404,6 +406,8 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
     TcArgs a;
     PrepJob pj;
     job_views(g, r, ws, pj, a);
+    a.fault = ctx->d_fault;
+    a.inject = ctx->inject.exchange(0);
     int rc = prep_jobs(ctx, &pj, 1, st);
     if (rc != BM_OK) return rc;
     const std::vector<int> ch = tc_choices(ctx, &g, &a, 1, st);
@@ -432,6 +436,7 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
         } else {
             PrepJob pj;
             job_views(gs[i], reqs[i], static_cast<char*>(ws) + offs[i], pj, args[i]);
+            args[i].fault = ctx->d_fault;
             pjs.push_back(pj);
             tc_ids.push_back(i);
         }
@@ -515,6 +520,28 @@ int get_stream_ws(bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out) {
 namespace bm {
 int ctx_device(const ::bm_ctx* ctx) { return ctx->device; }
 }  // namespace bm
+
+namespace {
+
+// Reads and clears the context's sticky timeout word (the caller has
+// synchronised the work it wants covered): BM_ERR_TIMEOUT naming the wait
+// site if a bounded device wait of the tensor-core kernel ran out.
+int take_fault(bm_ctx* ctx) {
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device fault word");
+    if (v == 0) return BM_OK;
+    if ((e = cudaMemset(ctx->d_fault, 0, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "clearing the device fault word");
+    static const char* const sites[] = {"?", "stage free", "accumulator free", "stage filled",
+                                        "accumulator filled", "A operand free", "tile staged",
+                                        "A operand formed"};
+    const int site = v - 0x100;
+    return fail(BM_ERR_TIMEOUT, std::string("a bounded device wait of the tensor-core kernel ran out (") +
+                                    (site >= 1 && site <= 7 ? sites[site] : "unknown site") + ")");
+}
+
+}  // namespace
 
 namespace {
 
@@ -678,7 +705,9 @@ int bm_create(bm_ctx** out, int device, size_t mem_budget_bytes, const char* tun
         load_tune_file(ctx);
     }
     DeviceGuard dg(device);
-    if ((e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+    if ((e = cudaMalloc(&ctx->d_fault, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_fault, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         delete ctx;
@@ -713,6 +742,7 @@ void bm_destroy(bm_ctx* ctx) {
     if (ctx->h_dev_img) cudaFree(ctx->h_dev_img);
     if (ctx->h_dev_out) cudaFree(ctx->h_dev_out);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->d_fault) cudaFree(ctx->d_fault);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
     for (int s = 0; s < bm_ctx::kSlots; ++s)
         if (ctx->slot_stream[s]) cudaStreamDestroy(ctx->slot_stream[s]);
@@ -720,6 +750,21 @@ void bm_destroy(bm_ctx* ctx) {
 }
 
 const char* bm_last_error(bm_ctx*) { return t_last_error.c_str(); }
+
+int bm_check(bm_ctx* ctx, bm_stream stream) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return take_fault(ctx);
+}
+
+int bm_set_fault_injection(bm_ctx* ctx, int mode) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    if (mode != 0 && mode != 1) return fail(BM_ERR_INVALID, "unknown fault injection mode");
+    ctx->inject.store(mode);
+    return BM_OK;
+}
 
 int bm_set_algo(bm_ctx* ctx, bm_algo algo) {
     if (!ctx) return fail(BM_ERR_INVALID, "null context");
@@ -780,7 +825,7 @@ int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dt
         (e = cudaMemcpyAsync(out_dist, d_dist, (size_t)g.nR * K * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
-    return BM_OK;
+    return take_fault(ctx);
 }
 
 int bm_match_batch(bm_ctx* ctx, const bm_request* reqs, int n, bm_stream stream) {

@@ -128,6 +128,8 @@ struct TcArgs {
     int32_t* pool_idx;        // float32: candidate pool offsets [nR][L]
     float* pool_score;        // float32: candidate pool scores  [nR][L]
     int* status;              // device error word (0 = ok)
+    int* fault = nullptr;     // nullable: context-wide sticky word, first timeout code kept
+    int inject = 0;           // test hook: 1 = the producer skips publishing its first stage
 };
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
 // Several jobs in persistent launches (consecutive jobs of one class share a

@@ -107,6 +107,8 @@ struct TcParams {
     TcGeom g;
     int njobs, total_tiles;
     int* status;
+    int* fault;   // nullable: sticky copy of the first timeout code (context-wide)
+    int inject;   // test hook: CTA 0's first producer skips publishing its first stage
     TcJob jobs[kMaxJobs];
 };
 
@@ -829,7 +831,10 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     }
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(BAR(k, kBarFull + stage));
+                // (the test hook withholds this arrival once: the MMA warp's bounded
+                // wait on the stage then runs out and the CTA takes its abort path)
+                const bool withhold = P.inject && cta == 0 && k == 0 && turn == 0 && c == 0;
+                if (lane == 0 && !withhold) mbar_arrive(BAR(k, kBarFull + stage));
             }
         }
         // drain the copies in flight before the shared memory is released:
@@ -1104,7 +1109,10 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicExch(P.status, 0x100 + *abort_flag);
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicExch(P.status, 0x100 + *abort_flag);
+        if (P.fault) atomicCAS(P.fault, 0, 0x100 + *abort_flag);
+    }
 }
 
 // Class geometry for a job shape: lane mapping, strips, slots, shared memory.
@@ -1329,6 +1337,8 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         const int choice = choices ? choices[i] : -1;
         if (!make_tc_geom(gs[i], P.g, choice)) return cudaErrorNotSupported;
         P.status = as[i].status;
+        P.fault = as[i].fault;
+        P.inject = as[i].inject;
         int tiles = 0, nj = 0;
         while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj]) &&
                (choices ? choices[i] : -1) == choice) {
