@@ -152,6 +152,18 @@ int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dt
                   int32_t* out_idx, void* out_dist);
 
 /*
+ * Host-buffer batch: n jobs whose img / out_idx / out_dist are HOST pointers
+ * (same fields and conventions as bm_match_batch otherwise).  Consecutive
+ * jobs are grouped in chunks (up to 16 jobs or 96 MB of staging) that run in
+ * two pipelines of (host-to-device copy, batched match, device-to-host copy)
+ * on the context's own streams, so the copies of one chunk overlap the
+ * matching of the next; the staging buffers are cached in the context.
+ * Returns after every result has landed (synchronous), with the check of
+ * bm_check.  Copies overlap only for page-locked host buffers.
+ */
+int bm_match_host_batch(bm_ctx* ctx, const bm_request* reqs, int n);
+
+/*
  * Match n independent jobs (any mix of sizes, channel counts, dtypes and
  * parameters) with one persistent launch per kernel stage, asynchronous on
  * `stream`.  Same per-job conventions as bm_match.  On a stream other than

@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
             "bm_match_direct": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_match_host": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp], ci),
             "bm_match_batch": ([vp, ctypes.POINTER(bm_request), ci, vp], ci),
+            "bm_match_host_batch": ([vp, ctypes.POINTER(bm_request), ci], ci),
             "bm_set_algo": ([vp, ci], ci),
             "bm_submit": ([vp, ctypes.POINTER(bm_request), ctypes.POINTER(ctypes.c_uint64)], ci),
             "bm_poll": ([vp, ctypes.c_uint64, pi, pi], ci),
@@ -194,6 +195,10 @@ def bm_nlm(ctx, img, H, W, C, dtype, patch, window, stride, b, out_est, out_thet
 def bm_match_host(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx, out_dist) -> int:
     return load().bm_match_host(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx,
                                 out_dist)
+
+
+def bm_match_host_batch(ctx, reqs, n) -> int:
+    return load().bm_match_host_batch(ctx, reqs, n)
 
 
 def bm_match_batch(ctx, reqs, n, stream) -> int:

@@ -162,6 +162,10 @@ struct bm_ctx {
     std::mutex host_mu;
     cudaStream_t host_stream = nullptr;
     void* h_dev_img = nullptr; size_t h_dev_img_bytes = 0;
+    // bm_match_host_batch: two pipelines (stream + device staging each)
+    cudaStream_t hb_stream[2] = {nullptr, nullptr};
+    void* hb_buf[2] = {nullptr, nullptr};
+    size_t hb_bytes[2] = {0, 0};
     void* h_dev_out = nullptr; size_t h_dev_out_bytes = 0;
     // serving
     static constexpr int kSlots = 4;
@@ -744,6 +748,10 @@ void bm_destroy(bm_ctx* ctx) {
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_fault) cudaFree(ctx->d_fault);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->hb_buf[b]) cudaFree(ctx->hb_buf[b]);
+        if (ctx->hb_stream[b]) cudaStreamDestroy(ctx->hb_stream[b]);
+    }
     for (int s = 0; s < bm_ctx::kSlots; ++s)
         if (ctx->slot_stream[s]) cudaStreamDestroy(ctx->slot_stream[s]);
     delete ctx;
@@ -825,6 +833,102 @@ int bm_match_host(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dt
         (e = cudaMemcpyAsync(out_dist, d_dist, (size_t)g.nR * K * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    return take_fault(ctx);
+}
+
+int bm_match_host_batch(bm_ctx* ctx, const bm_request* reqs, int n) {
+    if (!ctx) return fail(BM_ERR_INVALID, "null context");
+    if (n < 0 || (n > 0 && !reqs)) return fail(BM_ERR_INVALID, "bad request list");
+    std::vector<Geom> gs(n);
+    std::vector<size_t> in_b(n), out_b(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(reqs[i], gs[i]);
+        if (rc != BM_OK) return rc;
+        in_b[i] = align256((size_t)gs[i].H * gs[i].W * gs[i].C * (gs[i].dtype == kU8 ? 1 : 4));
+        out_b[i] = align256((size_t)gs[i].nR * gs[i].K * 4);
+    }
+    if (n == 0) return BM_OK;
+    std::lock_guard<std::mutex> lk(ctx->host_mu);
+    DeviceGuard dg(ctx->device);
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b)
+        if (!ctx->hb_stream[b] &&
+            (e = cudaStreamCreateWithFlags(&ctx->hb_stream[b], cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "stream create");
+    // chunks of consecutive jobs: up to 16 jobs or 96 MB of staging
+    constexpr int kChunkJobs = 16;
+    constexpr size_t kChunkBytes = (size_t)96 << 20;
+    std::vector<int> starts;
+    for (int i = 0; i < n;) {
+        starts.push_back(i);
+        size_t bytes = 0;
+        int m = 0;
+        while (i < n && m < kChunkJobs &&
+               (m == 0 || bytes + in_b[i] + 2 * out_b[i] <= kChunkBytes)) {
+            bytes += in_b[i] + 2 * out_b[i];
+            ++i;
+            ++m;
+        }
+    }
+    starts.push_back(n);
+    for (size_t c = 0; c + 1 < starts.size(); ++c) {
+        const int i0 = starts[c], i1 = starts[c + 1], m = i1 - i0, b = (int)(c & 1);
+        cudaStream_t st = ctx->hb_stream[b];
+        size_t stage = 0;
+        for (int i = i0; i < i1; ++i) stage += in_b[i] + 2 * out_b[i];
+        // staging of pipeline b: the previous chunk on this stream is done with
+        // it before anything below runs (stream order), but a reallocation
+        // must wait for it
+        if (ctx->hb_bytes[b] < stage) {
+            if (ctx->hb_buf[b]) {
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+                cudaFree(ctx->hb_buf[b]);
+                ctx->hb_buf[b] = nullptr;
+                ctx->hb_bytes[b] = 0;
+            }
+            if ((e = cudaMalloc(&ctx->hb_buf[b], stage)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+            ctx->hb_bytes[b] = stage;
+        }
+        char* base = static_cast<char*>(ctx->hb_buf[b]);
+        std::vector<bm_request> dr(reqs + i0, reqs + i1);
+        size_t off = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = i0 + k;
+            dr[k].img = base + off;
+            if ((e = cudaMemcpyAsync(base + off, reqs[i].img, in_b[i] > 0 ? (size_t)gs[i].H * gs[i].W * gs[i].C * (gs[i].dtype == kU8 ? 1 : 4) : 0,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "host-to-device copy");
+            off += in_b[i];
+            dr[k].out_idx = reinterpret_cast<int32_t*>(base + off);
+            off += out_b[i];
+            dr[k].out_dist = base + off;
+            off += out_b[i];
+        }
+        std::vector<size_t> offs(m);
+        size_t total = 0;
+        for (int k = 0; k < m; ++k) {
+            offs[k] = total;
+            total += align256(job_ws_bytes(ctx, gs[i0 + k]));
+        }
+        void* ws = nullptr;
+        if (total) {
+            int rc = get_stream_ws(ctx, st, total, &ws);
+            if (rc != BM_OK) return rc;
+        }
+        int rc = enqueue_batch(ctx, gs.data() + i0, dr.data(), m, ws, offs.data(), st, true);
+        if (rc != BM_OK) return rc;
+        for (int k = 0; k < m; ++k) {
+            const int i = i0 + k;
+            ctx->matches += 1;
+            ctx->refs += (unsigned long long)gs[i].nR;
+            const size_t ob = (size_t)gs[i].nR * gs[i].K * 4;
+            if ((e = cudaMemcpyAsync(reqs[i].out_idx, dr[k].out_idx, ob, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(reqs[i].out_dist, dr[k].out_dist, ob, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "device-to-host copy");
+        }
+    }
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaStreamSynchronize(ctx->hb_stream[b])) != cudaSuccess) return cuda_fail(e, "synchronize");
     return take_fault(ctx);
 }
 

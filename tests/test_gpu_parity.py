@@ -189,3 +189,24 @@ def test_float_error_bound_never_violated(ctx):
         run(ctx, make_image(H, W, 1, "f32", seed=40 + i), p, win, s, K, "selfconv")
     st = ctx.stats()
     assert st["bound_violations"] == 0, st
+
+
+def test_host_batch_equals_device_path(ctx):
+    # 20 mixed jobs from page-locked host buffers: more than one chunk, both pipelines
+    specs = [(100, 90, 1, "f32", 8, 39, 3, 16), (64, 64, 1, "u8", 8, 21, 1, 16),
+             (80, 72, 4, "u8", 8, 39, 3, 32), (150, 133, 1, "f32", 7, 61, 4, 70)] * 5
+    imgs, outs, reqs = [], [], []
+    for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
+        img = torch.from_numpy(make_image(H, W, C, dt, seed=90 + i)).pin_memory()
+        ny, nx = B.bm_num_refs(H, W, p, s)
+        idx = torch.full((ny * nx, K), -5, dtype=torch.int32).pin_memory()
+        dist = torch.full((ny * nx, K), -5, dtype=torch.int32 if dt == "u8" else torch.float32).pin_memory()
+        imgs.append(img)
+        outs.append((idx, dist))
+        reqs.append(B.Context.request(img, p, win, s, K, idx, dist))
+    arr = (B.bm_request * len(reqs))(*reqs)
+    assert B.bm_match_host_batch(ctx.handle, arr, len(reqs)) == B.BM_OK
+    for (H, W, C, dt, p, win, s, K), img, (idx, dist) in zip(specs, imgs, outs):
+        a, b = ctx.match(img.cuda(), p, win, s, K)
+        torch.cuda.synchronize()
+        assert torch.equal(a.cpu(), idx) and torch.equal(b.cpu(), dist)
