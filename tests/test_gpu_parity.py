@@ -210,3 +210,18 @@ def test_host_batch_equals_device_path(ctx):
         a, b = ctx.match(img.cuda(), p, win, s, K)
         torch.cuda.synchronize()
         assert torch.equal(a.cpu(), idx) and torch.equal(b.cpu(), dist)
+
+
+@pytest.mark.parametrize("dt", ["u8", "f32"])
+def test_largest_window_and_k(ctx, dt):
+    # window 127 (the largest odd window) with K = 128 (the largest K)
+    img = make_image(150, 140, 1, dt, seed=127)
+    gidx, gdist = run(ctx, img, 8, 127, 5, 128, "selfconv")
+    compare(img, 8, 127, 5, 128, gidx, gdist)
+
+
+def test_empty_batches(ctx):
+    arr = (B.bm_request * 1)()
+    assert B.bm_match_batch(ctx.handle, arr, 0, None) == B.BM_OK
+    assert B.bm_match_host_batch(ctx.handle, arr, 0) == B.BM_OK
+    assert B.bm_match_batch(ctx.handle, arr, -1, None) == B.BM_ERR_INVALID
