@@ -62,6 +62,8 @@ SMALL = [
     ("p16_f32",       50,  50, 1, "f32", 16, 9, 4,  8),
     ("stride5_f32",  101, 203, 1, "f32", 8, 39, 5, 16),
     ("tall_u8",      300,  40, 1, "u8",  8, 39, 3, 16),
+    ("c8_u8",         40,  36, 8, "u8",  5,  9, 2, 12),   # the largest channel count
+    ("c8_f32",        38,  35, 8, "f32", 4, 11, 3, 10),
 ]
 
 
@@ -101,6 +103,7 @@ FULL = [
     ("cfg4_1024x4_u8", 1024, 1024, 4, "u8", 8, 39, 3, 32, 4000),
     ("cfg3_1024_f32", 1024, 1024, 1, "f32", 7, 61, 4, 70, 3000),
     ("cfg1_64_u8", 64, 64, 1, "u8", 8, 21, 1, 16, 1000),
+    ("serve_2048_f32", 2048, 2048, 1, "f32", 8, 39, 3, 16, 5000),   # the largest serving side
 ]
 
 
