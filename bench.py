@@ -453,6 +453,52 @@ def match3d_throughput(ctx, synth, dev, stream, n=4):
                          "algorithmic_flop_per_image": flop}}
 
 
+def time_row_oracles(img, idx, synth, groups, nlm, ncc, m3d, seconds=1.0):
+    """The oracles of the rows beside block matching, as they stand, on bounded
+    seeded samples of the same workloads (one host thread, numpy): each result
+    dict gains "cpu_oracle" with the rate in the row's unit and the sample."""
+    from oracle import bm3d as O3
+    from oracle import groups as OG
+    from oracle import ncc as ON
+    from oracle import nlm as ONL
+    H, W, p, win, s, K = WL["H"], WL["W"], WL["patch"], WL["window"], WL["stride"], WL["K"]
+    ny, nx = (H - p) // s + 1, (W - p) // s + 1
+    rng = np.random.default_rng(SEED_BASE + 900)
+
+    def rate(fn, unit_count, what):
+        n, t0 = 0, time.perf_counter()
+        while True:
+            fn()
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                return {"value": unit_count * n / el, "cores": 1, "kind": "oracle",
+                        "sample": f"{what}, {n} run(s) in {el:.1f} s"}
+
+    if groups:
+        sel = np.sort(rng.choice(ny * nx, size=1000, replace=False))
+        sub = idx[sel]
+        g = OG.gather_groups(img, p, sub)
+        groups["cpu_oracle"] = {
+            "gather": rate(lambda: OG.gather_groups(img, p, sub), len(sel),
+                           "groups of 1000 seeded references of one 512x512 image (groups/s)"),
+            "aggregate": rate(lambda: OG.aggregate(g, sub, H, W, 1, p), len(sel),
+                              "reconstruction from those 1000 groups (groups/s)")}
+    if nlm:
+        refs = np.sort(rng.choice(ny * nx, size=100, replace=False))
+        nlm["cpu_oracle"] = rate(lambda: ONL.nlm(img, p, win, s, NLM_B, refs=refs), len(refs),
+                                 "100 seeded references of one 512x512 image (ref_patches/s)")
+    if ncc:
+        refs = np.sort(rng.choice(ny * nx, size=20, replace=False))
+        ncc["cpu_oracle"] = rate(lambda: ON.match_ncc(img, p, win, s, K, refs=refs), len(refs),
+                                 "20 seeded references of one 512x512 image (ref_patches/s)")
+    if m3d:
+        img4 = synth.rgbnir(H, W, 20.0, SEED_BASE + 300)
+        refs = np.sort(rng.choice(ny * nx * 3, size=20, replace=False))
+        m3d["cpu_oracle"] = rate(lambda: O3.match_3d(img4, p, 2, win, s, K, refs=refs), len(refs),
+                                 "20 seeded references of one 512x512x4 image (refs/s)")
+
+
 def run_ours(args, world, rank, local, dist):
     import torch
     import paper_2006_13714_gb300 as pkg
@@ -602,6 +648,7 @@ def run_ours(args, world, rank, local, dist):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        time_row_oracles(base[0], outs[0][0].cpu().numpy(), synth, groups, nlm, ncc, m3d)
         rate, cores, n_img, el = cpu_oracle_rate(args.cpu_seconds, SEED_BASE + 100)
         rate1, _, n1, el1 = cpu_oracle_rate(min(args.cpu_seconds, 5.0), SEED_BASE + 200, threads=1)
         cpu = {"value": rate, "unit": "ref_patches/s", "cores": cores, "kind": "oracle",
