@@ -13,11 +13,19 @@
 //
 // GB300 layout of the work (CUDA cores).  One block per 8 x 8 tile of the
 // spatial reference grid; the union of the tile's windows (all channels) is
-// staged in shared memory.  One warp per (reference, channel offset), one lane
-// per candidate; the reference patch sits in registers.  The warp keeps its K
-// best (distance, offset) keys one per lane in rank order; a round of 32
-// candidates costs one ballot against the K-th, and each candidate that beats
-// it is inserted at its rank (ballot count) with one shuffle of the list.
+// staged in shared memory channel-planar (plane stride 11 mod 32 words, row
+// pitch equal to the window width mod 32), so the lanes of a warp, holding
+// consecutive (column, channel offset) candidates, read distinct banks.  One
+// warp per (reference, channel offset).  A lane evaluates R = 4 vertically
+// adjacent candidates at once: per patch column and channel it loads the
+// P + R - 1 candidate values of that column once and the P reference values
+// (a broadcast), and forms R distances from them.  The reference therefore
+// stays in shared memory, registers stay low enough for two blocks per SM,
+// and the loads per candidate fall from p^2 d to (P + R - 1 + P) p d / R.
+// The warp keeps its K best (distance, offset) keys one per lane in rank
+// order; a ballot against the K-th screens 32 candidates, and each one that
+// beats it is inserted at its rank (ballot count) with one shuffle of the
+// list.
 #include "bm.h"
 #include "bm_internal.h"
 
@@ -29,10 +37,11 @@ namespace bm {
 namespace {
 
 constexpr int kTile3 = 8;
-constexpr int kThreads3 = 256;
+constexpr int kThreads3 = 384;
+constexpr int kRows3 = 4;  // vertically adjacent candidates evaluated by one lane
 constexpr int kMaxK3 = 32;
 constexpr int kMaxElems3 = 128;
-constexpr int kSmemLimit3 = 200 * 1024;
+constexpr int kSmemLimit3 = 200 * 1024;  // two blocks per SM up to 113 KB
 constexpr unsigned long long kEmpty3 = ~0ull;
 
 struct Bm3dParams {
@@ -42,19 +51,52 @@ struct Bm3dParams {
     int H, W, C, p, h, s, K, n_ry, n_rx, Hc, Wc, nc, tiles_x;
 };
 
+// Channel-plane stride for a plane of n words: n rounded up to 11 mod 32.
+__host__ __device__ __forceinline__ int plane_stride(int n) { return n + ((11 - (n & 31)) & 31); }
+// Region row pitch for n columns: n rounded up to the window width w mod 32.
+__host__ __device__ __forceinline__ int row_pitch(int n, int w) { return n + ((w - n) & 31); }
+
+// Inserts `key` into the warp's rank-ordered list (entry `lane`, K entries)
+// if it beats the K-th; `kth` follows the list.
+__device__ __forceinline__ void offer(unsigned long long key, unsigned long long& mine,
+                                      unsigned long long& kth, int lane, int K) {
+    unsigned mask = __ballot_sync(0xffffffffu, key < kth);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned long long b = __shfl_sync(0xffffffffu, key, src);
+        if (!(b < kth)) continue;  // the K-th moved past it
+        const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && mine < b));
+        const unsigned long long up = __shfl_up_sync(0xffffffffu, mine, 1);
+        if (lane == pos) mine = b;
+        else if (lane > pos) mine = up;
+        kth = __shfl_sync(0xffffffffu, mine, K - 1);
+    }
+}
+
 template <int P, int D, bool kU8>
-__global__ void __launch_bounds__(kThreads3) bm3d_kernel(const Bm3dParams Q) {
+__global__ void __launch_bounds__(kThreads3, 2) bm3d_kernel(const Bm3dParams Q) {
+    constexpr int R = kRows3, NW = P + R - 1;
     extern __shared__ __align__(16) float sreg[];
     const int ty = blockIdx.x / Q.tiles_x, tx = blockIdx.x - ty * Q.tiles_x;
     const int ry0 = ty * kTile3, rx0 = tx * kTile3;
     const int ry1 = min(ry0 + kTile3, Q.n_ry) - 1, rx1 = min(rx0 + kTile3, Q.n_rx) - 1;
     const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
     const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + P, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + P;
-    const int C = Q.C, nrow = Y1 - Y0, pitch = (X1 - X0) * C;
-    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
-        const int r = i / pitch, e = i - r * pitch;
-        const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
-        sreg[i] = kU8 ? (float)static_cast<const uint8_t*>(Q.img)[g] : static_cast<const float*>(Q.img)[g];
+    // R - 1 zero rows below the region: the last row group of a window reads
+    // them for candidates past its end, whose results are dropped.
+    const int C = Q.C, nrow = Y1 - Y0, srow = nrow + R - 1, gpitch = (X1 - X0) * C;
+    const int ncol = row_pitch(X1 - X0, 2 * Q.h + 1);  // words between region rows
+    const int ps = plane_stride(srow * ncol);          // words between channel planes
+    for (int i = threadIdx.x; i < srow * gpitch; i += blockDim.x) {
+        const int r = i / gpitch, e = i - r * gpitch;
+        const int x = e / C, c = e - x * C;
+        float v = 0.f;
+        if (r < nrow) {
+            const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
+            v = kU8 ? (float)static_cast<const uint8_t*>(Q.img)[g] : static_cast<const float*>(Q.img)[g];
+        }
+        sreg[c * ps + r * ncol + x] = v;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -64,53 +106,53 @@ __global__ void __launch_bounds__(kThreads3) bm3d_kernel(const Bm3dParams Q) {
         const int rs = rl / Q.nc, cr = rl - rs * Q.nc;
         const int ry = ry0 + rs / ntx, rx = rx0 + rs % ntx;
         const int yr = ry * Q.s, xr = rx * Q.s;
-        float ref[P][P][D];
-#pragma unroll
-        for (int u = 0; u < P; ++u)
-#pragma unroll
-            for (int v = 0; v < P; ++v)
-#pragma unroll
-                for (int t = 0; t < D; ++t)
-                    ref[u][v][t] = sreg[(yr + u - Y0) * pitch + (xr + v - X0) * C + cr + t];
+        const float* rb = sreg + cr * ps + (yr - Y0) * ncol + (xr - X0);
         const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
         const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
-        const int wx = cx1 - cx0 + 1, wxc = wx * Q.nc, ncand = (cy1 - cy0 + 1) * wxc;
+        const int wxc = (cx1 - cx0 + 1) * Q.nc;
+        const int nitem = ((cy1 - cy0 + R) / R) * wxc;  // (row group, column, channel offset)
         unsigned long long mine = kEmpty3, kth = kEmpty3;
-        for (int j0 = 0; j0 < ncand; j0 += 32) {
+        for (int j0 = 0; j0 < nitem; j0 += 32) {
             const int j = j0 + lane;
-            unsigned long long key = kEmpty3;
-            if (j < ncand) {
-                const int jy = j / wxc, rem = j - jy * wxc;
-                const int jx = rem / Q.nc, cc = rem - jx * Q.nc;
-                const int yc = cy0 + jy, xc = cx0 + jx;
-                const float* cb = sreg + (yc - Y0) * pitch + (xc - X0) * C + cc;
-                float s0 = 0.f, s1 = 0.f;
+            const bool live = j < nitem;
+            float acc[R];
 #pragma unroll
-                for (int u = 0; u < P; ++u)
+            for (int i = 0; i < R; ++i) acc[i] = 0.f;
+            int yc = cy0, xc = cx0, cc = 0;
+            if (live) {
+                const int jb = j / wxc, rem = j - jb * wxc;
+                const int jx = rem / Q.nc;
+                cc = rem - jx * Q.nc;
+                yc = cy0 + jb * R;
+                xc = cx0 + jx;
+                const float* cb = sreg + cc * ps + (yc - Y0) * ncol + (xc - X0);
 #pragma unroll
-                    for (int v = 0; v < P; ++v)
+                for (int t = 0; t < D; ++t)
 #pragma unroll
-                        for (int t = 0; t < D; ++t) {
-                            const float df = ref[u][v][t] - cb[u * pitch + v * C + t];
-                            if ((u * P + v) & 1) s1 = fmaf(df, df, s1);
-                            else s0 = fmaf(df, df, s0);
-                        }
-                const float d = s0 + s1;
-                const unsigned off = (unsigned)((yc * Q.W + xc) * C + cc);
-                key = kU8 ? ((unsigned long long)(unsigned)d << 32) | off
-                          : ((unsigned long long)__float_as_uint(d) << 32) | off;
+                    for (int v = 0; v < P; ++v) {
+                        float w[NW], rr[P];
+#pragma unroll
+                        for (int u = 0; u < NW; ++u) w[u] = cb[t * ps + u * ncol + v];
+#pragma unroll
+                        for (int u = 0; u < P; ++u) rr[u] = rb[t * ps + u * ncol + v];
+#pragma unroll
+                        for (int u = 0; u < P; ++u)
+#pragma unroll
+                            for (int i = 0; i < R; ++i) {
+                                const float df = rr[u] - w[u + i];
+                                acc[i] = fmaf(df, df, acc[i]);
+                            }
+                    }
             }
-            unsigned mask = __ballot_sync(0xffffffffu, key < kth);
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const unsigned long long b = __shfl_sync(0xffffffffu, key, src);
-                if (!(b < kth)) continue;  // the K-th moved past it
-                const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && mine < b));
-                const unsigned long long up = __shfl_up_sync(0xffffffffu, mine, 1);
-                if (lane == pos) mine = b;
-                else if (lane > pos) mine = up;
-                kth = __shfl_sync(0xffffffffu, mine, K - 1);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                unsigned long long key = kEmpty3;
+                if (live && yc + i <= cy1) {
+                    const unsigned off = (unsigned)(((yc + i) * Q.W + xc) * C + cc);
+                    key = kU8 ? ((unsigned long long)(unsigned)acc[i] << 32) | off
+                              : ((unsigned long long)__float_as_uint(acc[i]) << 32) | off;
+                }
+                offer(key, mine, kth, lane, K);
             }
         }
         if (lane < K) {
@@ -187,7 +229,8 @@ int bm_match_3d(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtyp
     const int tiles = ((Q.n_ry + kTile3 - 1) / kTile3) * Q.tiles_x;
     const int rows = std::min(H, (kTile3 - 1) * stride + 2 * Q.h + patch);
     const int cols = std::min(W, (kTile3 - 1) * stride + 2 * Q.h + patch);
-    const size_t smem = (size_t)rows * cols * C * sizeof(float);
+    const size_t smem =
+        (size_t)plane_stride((rows + kRows3 - 1) * row_pitch(cols, 2 * Q.h + 1)) * C * sizeof(float);
     if (smem > (size_t)kSmemLimit3)
         return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");
     DevGuard dg(ctx_device(ctx));

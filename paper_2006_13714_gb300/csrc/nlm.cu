@@ -13,7 +13,9 @@
 // 8 x 8 references; the image region their windows cover is staged in shared
 // memory as element pairs (pair e of a row holds elements e and e + 1), so a
 // patch row starting anywhere is read with 64-bit loads and processed two
-// elements at a time with packed FP32 arithmetic (sub/fma.rn.f32x2).  One
+// elements at a time with packed FP32 arithmetic (sub/fma.rn.f32x2).  The
+// region's row pitch is the window width times C mod 16 pairs: 32 candidates
+// that wrap onto the next window row still read distinct banks.  One
 // warp per reference, one lane per candidate (strided over the window): the
 // lane forms the distance, its weight (ex2), and adds the weighted candidate
 // into its register copy of the estimate; a butterfly over the warp sums the
@@ -61,21 +63,22 @@ __global__ void __launch_bounds__(kNlmThreads) nlm_kernel(const NlmParams Q) {
     // region: every candidate patch of the tile's windows
     const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
     const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + P, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + P;
-    const int nrow = Y1 - Y0, pitch = (X1 - X0) * C;  // pairs per region row
-    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
-        const int r = i / pitch, e = i - r * pitch;
+    const int nrow = Y1 - Y0, width = (X1 - X0) * C;  // pairs per region row
+    const int pitch = width + (((2 * Q.h + 1) * C - width) & 15);  // padded row pitch
+    for (int i = threadIdx.x; i < nrow * width; i += blockDim.x) {
+        const int r = i / width, e = i - r * width;
         const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
         float a, b;
         if (Q.dtype == kU8) {
             const uint8_t* im = static_cast<const uint8_t*>(Q.img);
             a = im[g];
-            b = e + 1 < pitch ? im[g + 1] : 0.f;
+            b = e + 1 < width ? im[g + 1] : 0.f;
         } else {
             const float* im = static_cast<const float*>(Q.img);
             a = im[g];
-            b = e + 1 < pitch ? im[g + 1] : 0.f;
+            b = e + 1 < width ? im[g + 1] : 0.f;
         }
-        sreg[i] = make_float2(a, b);
+        sreg[r * pitch + e] = make_float2(a, b);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -99,8 +102,8 @@ __global__ void __launch_bounds__(kNlmThreads) nlm_kernel(const NlmParams Q) {
         for (int j = lane; j < ncand; j += 32) {
             const int jy = j / wx, jx = j - jy * wx;
             const float2* cb = sreg + (cy0 + jy - Y0) * pitch + (cx0 + jx - X0) * C;
-            // distance, two elements at a time
-            unsigned long long dd = 0ull;
+            // distance, two elements at a time, in two chains (even / odd patch rows)
+            unsigned long long dd[2] = {0ull, 0ull};
             float dt = 0.f;
 #pragma unroll
             for (int u = 0; u < P; ++u) {
@@ -108,15 +111,15 @@ __global__ void __launch_bounds__(kNlmThreads) nlm_kernel(const NlmParams Q) {
                 for (int t = 0; t < NPR; ++t) {
                     unsigned long long df;
                     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(pk(rb[u * pitch + 2 * t])), "l"(pk(cb[u * pitch + 2 * t])));
-                    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(dd) : "l"(df));
+                    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(dd[u & 1]) : "l"(df));
                 }
                 if (TAIL) {
                     const float df = rb[u * pitch + PC - 1].x - cb[u * pitch + PC - 1].x;
                     dt = fmaf(df, df, dt);
                 }
             }
-            const float2 d2 = upk(dd);
-            const float d = (d2.x + d2.y) + dt;
+            const float2 d2 = upk(dd[0]), d3 = upk(dd[1]);
+            const float d = ((d2.x + d2.y) + (d3.x + d3.y)) + dt;
             const float w = exp2f(-d * Q.k2);
             theta += w;
             const unsigned long long ww = pk(make_float2(w, w));
@@ -225,7 +228,7 @@ int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, in
     for (; t >= 1; t /= 2) {
         const int rows = std::min(H, (t - 1) * stride + 2 * Q.h + patch);
         const int cols = std::min(W, (t - 1) * stride + 2 * Q.h + patch);
-        bytes = (size_t)rows * cols * C * sizeof(float2);
+        bytes = (size_t)rows * (cols * C + 15) * sizeof(float2);
         if (bytes <= (size_t)kNlmSmemLimit) break;
     }
     if (t < 1) return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");
