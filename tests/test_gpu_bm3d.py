@@ -75,6 +75,14 @@ CASES = [
     ("u8_c2_d1_k", 20,  22, 2, "u8",  3, 1, 3,  2, 32),
     ("f32_c3_d2",  40,  42, 3, "f32", 4, 2, 13, 3, 16),
     ("f32_c2_d1",  44,  40, 2, "f32", 7, 1, 21, 4, 10),
+    # uint8 with a patch side of 4 or 8 takes the integer (dp4a) kernel:
+    # windows shorter than its 8-row candidate groups, one channel offset
+    # (two-row tiles), ragged borders, K at its limit
+    ("u8_c2_d1_p8_w7",  29, 35, 2, "u8", 8, 1, 7,  2, 20),
+    ("u8_c1_d1_p4",     33, 30, 1, "u8", 4, 1, 13, 1, 32),
+    ("u8_c4_d3_p4",     27, 38, 4, "u8", 4, 3, 17, 2, 32),
+    ("u8_c3_d2_p8_s5",  45, 41, 3, "u8", 8, 2, 23, 5, 9),
+    ("f32_c4_d2_p8",    36, 34, 4, "f32", 8, 2, 15, 3, 16),
 ]
 
 
@@ -82,6 +90,16 @@ CASES = [
 def test_small_full_parity(ctx, case):
     name, H, W, C, dt, p, d, win, s, K = case
     check(ctx, make_image(H, W, C, dt, seed=H + W * 5 + C), p, d, win, s, K)
+
+
+def test_saturated_values(ctx):
+    # only 0 and 255: the largest squared differences (every partial sum of
+    # the integer kernel near its top) and many equal distances, which the
+    # offset must order
+    rng = np.random.default_rng(77)
+    img = np.ascontiguousarray((rng.random((30, 34, 3)) < 0.5).astype(np.uint8) * 255)
+    check(ctx, img, 8, 2, 11, 2, 24)
+    check(ctx, img, 4, 3, 9, 1, 32)
 
 
 def test_full_size_sampled_parity(ctx):
