@@ -387,8 +387,11 @@ def nlm_throughput(ctx, imgs, stream, dev, pairs, n=16):
 
 def ncc_throughput(ctx, imgs, stream, dev, pairs, n=16):
     """NCC block matching (Eq. equ:cor) on n images of the workload (K 16),
-    CUDA events on the launch stream.  Roofline: ALU (FP32), 4 p^2 C FLOP per
-    pair (cross term and candidate norm) against the nominal FP32 FMA rate."""
+    CUDA events on the launch stream.  Roofline: ALU (FP32) against the
+    nominal FP32 FMA rate; the work is the cross term, 2 p^2 C FLOP per pair,
+    plus one norm (2 p^2 C FLOP) per patch position of the image: a
+    candidate's norm does not depend on the reference, and the kernel forms
+    it once."""
     import torch
     H, W, p, win, s, K = WL["H"], WL["W"], WL["patch"], WL["window"], WL["stride"], WL["K"]
     ny, nx = (H - p) // s + 1, (W - p) // s + 1
@@ -406,7 +409,7 @@ def ncc_throughput(ctx, imgs, stream, dev, pairs, n=16):
         if rep:
             times.append(e0.elapsed_time(e1) / n)
     ms = min(times)
-    flop = 4.0 * pairs * p * p
+    flop = 2.0 * pairs * p * p + 2.0 * (H - p + 1) * (W - p + 1) * p * p
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = flop / (ms / 1e3) / 1e12
     return {"images": n, "us_per_image": 1e3 * ms, "ref_patches_per_s": ny * nx / (ms / 1e3),

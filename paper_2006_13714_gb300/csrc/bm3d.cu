@@ -62,24 +62,6 @@ __host__ __device__ __forceinline__ int plane_stride(int n) { return n + ((11 - 
 // Region row pitch for n columns: n rounded up to the window width w mod 32.
 __host__ __device__ __forceinline__ int row_pitch(int n, int w) { return n + ((w - n) & 31); }
 
-// Inserts `key` into the warp's rank-ordered list (entry `lane`, K entries)
-// if it beats the K-th; `kth` follows the list.
-__device__ __forceinline__ void offer(unsigned long long key, unsigned long long& mine,
-                                      unsigned long long& kth, int lane, int K) {
-    unsigned mask = __ballot_sync(0xffffffffu, key < kth);
-    while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const unsigned long long b = __shfl_sync(0xffffffffu, key, src);
-        if (!(b < kth)) continue;  // the K-th moved past it
-        const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && mine < b));
-        const unsigned long long up = __shfl_up_sync(0xffffffffu, mine, 1);
-        if (lane == pos) mine = b;
-        else if (lane > pos) mine = up;
-        kth = __shfl_sync(0xffffffffu, mine, K - 1);
-    }
-}
-
 template <int P, int D, bool kU8>
 __global__ void __launch_bounds__(kThreads3, 2) bm3d_kernel(const Bm3dParams Q) {
     constexpr int R = kRows3, NW = P + R - 1;
@@ -158,7 +140,7 @@ __global__ void __launch_bounds__(kThreads3, 2) bm3d_kernel(const Bm3dParams Q) 
                     key = kU8 ? ((unsigned long long)(unsigned)acc[i] << 32) | off
                               : ((unsigned long long)__float_as_uint(acc[i]) << 32) | off;
                 }
-                offer(key, mine, kth, lane, K);
+                warp_list_offer(key, mine, kth, lane, K);
             }
         }
         if (lane < K) {
@@ -302,7 +284,7 @@ __global__ void __launch_bounds__(kThreadsI, 2) bm3d_u8_kernel(const Bm3dParams 
                     const unsigned off = (unsigned)(((yc + i) * Q.W + xc) * C + cc);
                     key = ((unsigned long long)d << 32) | off;
                 }
-                offer(key, mine, kth, lane, K);
+                warp_list_offer(key, mine, kth, lane, K);
             }
         }
         if (lane < K) {

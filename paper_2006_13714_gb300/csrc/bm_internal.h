@@ -38,6 +38,28 @@ __device__ __forceinline__ int fast_div(int n, const FastDiv& f) {
     return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
 }
 
+// A warp's top-K list of 64-bit keys, smaller is better: lane i holds entry
+// i in rank order (lanes >= K hold nothing of use) and `kth` is entry K - 1
+// on every lane (all ones while the list is not full).  offer() screens the
+// 32 lanes' keys with one ballot against the K-th and inserts each one that
+// still beats it at its rank (a ballot count) with one shuffle of the list.
+// Every lane of the warp must call it.
+__device__ __forceinline__ void warp_list_offer(unsigned long long key, unsigned long long& mine,
+                                                unsigned long long& kth, int lane, int K) {
+    unsigned mask = __ballot_sync(0xffffffffu, key < kth);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned long long b = __shfl_sync(0xffffffffu, key, src);
+        if (!(b < kth)) continue;  // the K-th moved past it
+        const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && mine < b));
+        const unsigned long long up = __shfl_up_sync(0xffffffffu, mine, 1);
+        if (lane == pos) mine = b;
+        else if (lane > pos) mine = up;
+        kth = __shfl_sync(0xffffffffu, mine, K - 1);
+    }
+}
+
 // Device ordinal of a context (bm_api.cu).
 int ctx_device(const ::bm_ctx* ctx);
 

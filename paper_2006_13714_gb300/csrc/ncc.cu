@@ -15,12 +15,16 @@
 // references; the union of the tile's windows is staged in shared memory.
 //   Fast path (K <= 32, instantiated patch shapes with p*p*C <= 64): the
 //   region is stored as element pairs (pair e of a row holds elements e and
-//   e + 1) and read with 64-bit loads; one warp per reference, one lane per
-//   candidate, cross term and norm two elements at a time with packed FP32
-//   (fma.rn.f32x2).  The warp keeps the K best candidates one per lane, in
-//   order; a round of 32 new candidates costs one ballot against the K-th,
-//   and each candidate that beats it is inserted at its rank (ballot count)
-//   with one shuffle of the list.
+//   e + 1) and read with 64-bit loads.  The norms ||X_j||^2 of all patch
+//   positions of the region are formed once per block (they do not depend on
+//   the reference) and kept beside it.  One warp per reference, one lane per
+//   candidate: the cross term two elements at a time with packed FP32
+//   (fma.rn.f32x2), in two chains.  The warp keeps the K best candidates one
+//   per lane, in order; a round of 32 new candidates costs one ballot against
+//   the K-th, and each candidate that beats it is inserted at its rank
+//   (ballot count) with one shuffle of the list.  float32 ranks one 64-bit
+//   key per candidate (order-preserving score bits above the offset); uint8
+//   keeps (a, n, offset) for its exact comparison.
 //   General path: one thread per reference, its K best in a max-heap (worst
 //   at the root) in shared memory.
 #include "bm.h"
@@ -37,6 +41,7 @@ constexpr int kNccTile = 8;
 constexpr int kNccThreads = kNccTile * kNccTile;
 constexpr int kNccMaxK = 64;
 constexpr int kNccSmemLimit = 200 * 1024;
+constexpr int kNccRows = 4;  // fast path: vertically adjacent candidates per lane
 
 struct NccParams {
     const void* img;
@@ -179,8 +184,10 @@ __global__ void __launch_bounds__(kNccThreads) ncc_kernel(const NccParams Q) {
 
 // ---------------------------------------------------------------- fast path
 
-__device__ __forceinline__ unsigned long long pk2(float2 v) {
-    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+// An element pair straight from shared memory into a 64-bit register (the
+// operand form of the packed FP32 instructions).
+__device__ __forceinline__ unsigned long long ld2(const float2* q) {
+    return *reinterpret_cast<const unsigned long long*>(q);
 }
 __device__ __forceinline__ float sum2(unsigned long long v) {
     return __uint_as_float((unsigned)v) + __uint_as_float((unsigned)(v >> 32));
@@ -189,27 +196,53 @@ __device__ __forceinline__ float sum2(unsigned long long v) {
 template <int P, int C, bool kU8>
 __global__ void __launch_bounds__(256) ncc_warp_kernel(const NccParams Q) {
     constexpr int PC = P * C, NPR = PC / 2, TAIL = PC & 1;
+    constexpr int R = kNccRows, NW = P + R - 1;
     extern __shared__ __align__(16) float2 sp[];
     const int ty = blockIdx.x / Q.tiles_x, tx = blockIdx.x - ty * Q.tiles_x;
     const int ry0 = ty * kNccTile, rx0 = tx * kNccTile;
     const int ry1 = min(ry0 + kNccTile, Q.n_ry) - 1, rx1 = min(rx0 + kNccTile, Q.n_rx) - 1;
     const int Y0 = max(0, ry0 * Q.s - Q.h), X0 = max(0, rx0 * Q.s - Q.h);
     const int Y1 = min(Q.Hc - 1, ry1 * Q.s + Q.h) + P, X1 = min(Q.Wc - 1, rx1 * Q.s + Q.h) + P;
-    const int nrow = Y1 - Y0, pitch = (X1 - X0) * C;
-    for (int i = threadIdx.x; i < nrow * pitch; i += blockDim.x) {
+    // R - 1 zero rows below the region: the last row group of a window reads
+    // them for candidates past its end, whose results are dropped
+    const int nrow = Y1 - Y0, srow = nrow + R - 1, pitch = (X1 - X0) * C;
+    for (int i = threadIdx.x; i < srow * pitch; i += blockDim.x) {
         const int r = i / pitch, e = i - r * pitch;
-        const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
-        float a, b;
-        if (kU8) {
-            const uint8_t* im = static_cast<const uint8_t*>(Q.img);
-            a = im[g];
-            b = e + 1 < pitch ? im[g + 1] : 0.f;
-        } else {
-            const float* im = static_cast<const float*>(Q.img);
-            a = im[g];
-            b = e + 1 < pitch ? im[g + 1] : 0.f;
+        float a = 0.f, b = 0.f;
+        if (r < nrow) {
+            const size_t g = ((size_t)(Y0 + r) * Q.W + X0) * C + e;
+            if (kU8) {
+                const uint8_t* im = static_cast<const uint8_t*>(Q.img);
+                a = im[g];
+                b = e + 1 < pitch ? im[g + 1] : 0.f;
+            } else {
+                const float* im = static_cast<const float*>(Q.img);
+                a = im[g];
+                b = e + 1 < pitch ? im[g + 1] : 0.f;
+            }
         }
         sp[i] = make_float2(a, b);
+    }
+    __syncthreads();
+    // ||X_j||^2 of every patch position of the region, once per block (it
+    // does not depend on the reference)
+    const int npy = nrow - P + 1, npx = X1 - X0 - P + 1;
+    float* snorm = reinterpret_cast<float*>(sp + srow * pitch);
+    for (int i = threadIdx.x; i < npy * npx; i += blockDim.x) {
+        const int y = i / npx, x = i - y * npx;
+        const float2* cb = sp + y * pitch + x * C;
+        unsigned long long n2 = 0ull;
+        float nt = 0.f;
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+#pragma unroll
+            for (int t = 0; t < NPR; ++t) {
+                const unsigned long long c2 = ld2(&cb[u * pitch + 2 * t]);
+                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(n2) : "l"(c2));
+            }
+            if (TAIL) nt = fmaf(cb[u * pitch + PC - 1].x, cb[u * pitch + PC - 1].x, nt);
+        }
+        snorm[i] = sum2(n2) + nt;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -219,87 +252,146 @@ __global__ void __launch_bounds__(256) ncc_warp_kernel(const NccParams Q) {
         const int ry = ry0 + rl / ntx, rx = rx0 + rl % ntx;
         const int yr = ry * Q.s, xr = rx * Q.s;
         const float2* rb = sp + (yr - Y0) * pitch + (xr - X0) * C;
-        unsigned long long nr2 = 0ull;
-        float nrt = 0.f;
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-#pragma unroll
-            for (int t = 0; t < NPR; ++t) {
-                const unsigned long long r2 = pk2(rb[u * pitch + 2 * t]);
-                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(nr2) : "l"(r2));
-            }
-            if (TAIL) nrt = fmaf(rb[u * pitch + PC - 1].x, rb[u * pitch + PC - 1].x, nrt);
-        }
-        const float nr = sum2(nr2) + nrt;
+        const float nr = snorm[(yr - Y0) * npx + (xr - X0)];
         const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
         const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
-        const int wx = cx1 - cx0 + 1, ncand = (cy1 - cy0 + 1) * wx;
-        // the list: entry `lane` (in rank order; lanes >= K hold nothing of use)
-        Ent mine{0.f, 1.f, -1};
-        Ent kth{0.f, 1.f, -1};
-        for (int j0 = 0; j0 < ncand; j0 += 32) {
-            const int j = j0 + lane;
-            Ent c{0.f, 1.f, -1};
-            if (j < ncand) {
-                const int jy = j / wx, jx = j - jy * wx;
-                const int yc = cy0 + jy, xc = cx0 + jx;
-                const float2* cb = sp + (yc - Y0) * pitch + (xc - X0) * C;
-                unsigned long long a2 = 0ull, n2 = 0ull;
-                float at = 0.f, nt = 0.f;
+        const int wx = cx1 - cx0 + 1;
+        const int nitem = ((cy1 - cy0 + R) / R) * wx;  // (row group, column)
+        // cross terms <X_r, X_j> of the R candidates (yc + i, xc), i < R: each
+        // window row loaded serves up to R of them, the reference by broadcast
+        auto cross = [&](int yc, int xc, float (&a)[R]) {
+            const float2* cb = sp + (yc - Y0) * pitch + (xc - X0) * C;
+            unsigned long long a2[R];
+            float at[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                a2[i] = 0ull;
+                at[i] = 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < NPR; ++t) {
+                unsigned long long w[NW];
+#pragma unroll
+                for (int u = 0; u < NW; ++u) w[u] = ld2(&cb[u * pitch + 2 * t]);
 #pragma unroll
                 for (int u = 0; u < P; ++u) {
+                    const unsigned long long r2 = ld2(&rb[u * pitch + 2 * t]);
 #pragma unroll
-                    for (int t = 0; t < NPR; ++t) {
-                        const unsigned long long c2 = pk2(cb[u * pitch + 2 * t]);
-                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2) : "l"(pk2(rb[u * pitch + 2 * t])), "l"(c2));
-                        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(n2) : "l"(c2));
-                    }
-                    if (TAIL) {
-                        const float cv = cb[u * pitch + PC - 1].x;
-                        at = fmaf(rb[u * pitch + PC - 1].x, cv, at);
-                        nt = fmaf(cv, cv, nt);
-                    }
-                }
-                const float a = sum2(a2) + at, n = sum2(n2) + nt;
-                c.off = yc * Q.W + xc;
-                if (kU8) {
-                    const bool z = n == 0.f || nr == 0.f;
-                    c.a = z ? 0.f : a;
-                    c.n = z ? 1.f : n;
-                } else {
-                    c.a = (n > 0.f && nr > 0.f) ? a * rsqrtf(n) : 0.f;
+                    for (int i = 0; i < R; ++i)
+                        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i]) : "l"(r2), "l"(w[u + i]));
                 }
             }
-            unsigned mask = __ballot_sync(0xffffffffu, c.off >= 0 && better<kU8>(c, kth));
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                Ent b;
-                b.a = __shfl_sync(0xffffffffu, c.a, src);
-                b.n = __shfl_sync(0xffffffffu, c.n, src);
-                b.off = __shfl_sync(0xffffffffu, c.off, src);
-                if (!better<kU8>(b, kth)) continue;  // the K-th moved past it
-                const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && better<kU8>(mine, b)));
-                Ent up;
-                up.a = __shfl_up_sync(0xffffffffu, mine.a, 1);
-                up.n = __shfl_up_sync(0xffffffffu, mine.n, 1);
-                up.off = __shfl_up_sync(0xffffffffu, mine.off, 1);
-                if (lane == pos) mine = b;
-                else if (lane > pos) mine = up;
-                kth.a = __shfl_sync(0xffffffffu, mine.a, K - 1);
-                kth.n = __shfl_sync(0xffffffffu, mine.n, K - 1);
-                kth.off = __shfl_sync(0xffffffffu, mine.off, K - 1);
+            if (TAIL) {
+                float w[NW];
+#pragma unroll
+                for (int u = 0; u < NW; ++u) w[u] = cb[u * pitch + PC - 1].x;
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    const float rv = rb[u * pitch + PC - 1].x;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) at[i] = fmaf(rv, w[u + i], at[i]);
+                }
             }
-        }
-        if (lane < K) {
-            const size_t ref = (size_t)ry * Q.n_rx + rx;
-            float sc = -__int_as_float(0x7f800000);
-            if (mine.off >= 0) {
-                if (kU8) sc = nr > 0.f ? (float)((double)mine.a / sqrt((double)nr * (double)mine.n)) : 0.f;
-                else sc = nr > 0.f ? mine.a * rsqrtf(nr) : 0.f;
+#pragma unroll
+            for (int i = 0; i < R; ++i) a[i] = sum2(a2[i]) + at[i];
+        };
+        const size_t ref = (size_t)ry * Q.n_rx + rx;
+        if constexpr (!kU8) {
+            // float32: the rank is (score, offset), one 64-bit key per candidate,
+            // smaller is better: the score's order-preserving bits, complemented,
+            // above the offset
+            unsigned long long mine = ~0ull, kth = ~0ull;
+            for (int j0 = 0; j0 < nitem; j0 += 32) {
+                const int j = j0 + lane;
+                const bool live = j < nitem;
+                float a[R];
+                int yc = cy0, xc = cx0;
+                if (live) {
+                    const int jb = j / wx;
+                    yc = cy0 + jb * R;
+                    xc = cx0 + j - jb * wx;
+                    cross(yc, xc, a);
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    unsigned long long key = ~0ull;
+                    if (live && yc + i <= cy1) {
+                        const float n = snorm[(yc + i - Y0) * npx + (xc - X0)];
+                        // + 0.f makes a zero score +0 (-0 would order below it)
+                        const float sc = ((n > 0.f && nr > 0.f) ? a[i] * rsqrtf(n) : 0.f) + 0.f;
+                        const unsigned b = __float_as_uint(sc);
+                        const unsigned ord = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+                        key = ((unsigned long long)~ord << 32) | (unsigned)((yc + i) * Q.W + xc);
+                    }
+                    warp_list_offer(key, mine, kth, lane, K);
+                }
             }
-            Q.out_idx[ref * K + lane] = mine.off;
-            Q.out_score[ref * K + lane] = sc;
+            if (lane < K) {
+                float sc = -__int_as_float(0x7f800000);
+                int off = -1;
+                if (mine != ~0ull) {
+                    const unsigned ord = ~(unsigned)(mine >> 32);
+                    const float s = __uint_as_float((ord & 0x80000000u) ? (ord & 0x7fffffffu) : ~ord);
+                    sc = nr > 0.f ? s * rsqrtf(nr) : 0.f;
+                    off = (int)(unsigned)mine;
+                }
+                Q.out_idx[ref * K + lane] = off;
+                Q.out_score[ref * K + lane] = sc;
+            }
+        } else {
+            // uint8: exact ranking through a^2 n products, (a, n, offset) per entry
+            Ent mine{0.f, 1.f, -1};  // entry `lane` in rank order (lanes >= K: nothing of use)
+            Ent kth{0.f, 1.f, -1};
+            for (int j0 = 0; j0 < nitem; j0 += 32) {
+                const int j = j0 + lane;
+                const bool live = j < nitem;
+                float a[R];
+                int yc = cy0, xc = cx0;
+                if (live) {
+                    const int jb = j / wx;
+                    yc = cy0 + jb * R;
+                    xc = cx0 + j - jb * wx;
+                    cross(yc, xc, a);
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    Ent c{0.f, 1.f, -1};
+                    if (live && yc + i <= cy1) {
+                        const float n = snorm[(yc + i - Y0) * npx + (xc - X0)];
+                        c.off = (yc + i) * Q.W + xc;
+                        const bool z = n == 0.f || nr == 0.f;
+                        c.a = z ? 0.f : a[i];
+                        c.n = z ? 1.f : n;
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, c.off >= 0 && better<true>(c, kth));
+                    while (mask) {
+                        const int src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        Ent b;
+                        b.a = __shfl_sync(0xffffffffu, c.a, src);
+                        b.n = __shfl_sync(0xffffffffu, c.n, src);
+                        b.off = __shfl_sync(0xffffffffu, c.off, src);
+                        if (!better<true>(b, kth)) continue;  // the K-th moved past it
+                        const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && better<true>(mine, b)));
+                        Ent up;
+                        up.a = __shfl_up_sync(0xffffffffu, mine.a, 1);
+                        up.n = __shfl_up_sync(0xffffffffu, mine.n, 1);
+                        up.off = __shfl_up_sync(0xffffffffu, mine.off, 1);
+                        if (lane == pos) mine = b;
+                        else if (lane > pos) mine = up;
+                        kth.a = __shfl_sync(0xffffffffu, mine.a, K - 1);
+                        kth.n = __shfl_sync(0xffffffffu, mine.n, K - 1);
+                        kth.off = __shfl_sync(0xffffffffu, mine.off, K - 1);
+                    }
+                }
+            }
+            if (lane < K) {
+                float sc = -__int_as_float(0x7f800000);
+                if (mine.off >= 0)
+                    sc = nr > 0.f ? (float)((double)mine.a / sqrt((double)nr * (double)mine.n)) : 0.f;
+                Q.out_idx[ref * K + lane] = mine.off;
+                Q.out_score[ref * K + lane] = sc;
+            }
         }
     }
 }
@@ -362,9 +454,12 @@ int bm_match_ncc(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dty
     const int rows = std::min(H, (kNccTile - 1) * stride + 2 * Q.h + patch);
     const int cols = std::min(W, (kNccTile - 1) * stride + 2 * Q.h + patch);
     const size_t region = (size_t)rows * cols * C;
+    // fast path: the region as element pairs, then the norms of its patch positions
+    const size_t fast_bytes = (size_t)(rows + kNccRows - 1) * cols * C * sizeof(float2) +
+                              (size_t)(rows - patch + 1) * (cols - patch + 1) * sizeof(float);
     NccKernel fast = K <= 32 ? pick_fast(patch, C, Q.dtype == kU8) : nullptr;
-    if (fast && region * sizeof(float2) > (size_t)kNccSmemLimit) fast = nullptr;
-    const size_t smem = fast ? region * sizeof(float2)
+    if (fast && fast_bytes > (size_t)kNccSmemLimit) fast = nullptr;
+    const size_t smem = fast ? fast_bytes
                              : ((region * 4 + 15) & ~size_t(15)) + (size_t)K * kNccThreads * sizeof(Ent);
     if (smem > (size_t)kNccSmemLimit)
         return set_error(BM_ERR_UNSUPPORTED, "search region does not fit in shared memory");

@@ -48,6 +48,11 @@ struct NlmParams {
 __device__ __forceinline__ unsigned long long pk(float2 v) {
     return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
 }
+// An element pair straight from shared memory into a 64-bit register (the
+// operand form of the packed FP32 instructions).
+__device__ __forceinline__ unsigned long long ld2(const float2* q) {
+    return *reinterpret_cast<const unsigned long long*>(q);
+}
 __device__ __forceinline__ float2 upk(unsigned long long v) {
     return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
 }
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__(kNlmThreads) nlm_kernel(const NlmParams Q) {
 #pragma unroll
                 for (int t = 0; t < NPR; ++t) {
                     unsigned long long df;
-                    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(pk(rb[u * pitch + 2 * t])), "l"(pk(cb[u * pitch + 2 * t])));
+                    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(ld2(&rb[u * pitch + 2 * t])), "l"(ld2(&cb[u * pitch + 2 * t])));
                     asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(dd[u & 1]) : "l"(df));
                 }
                 if (TAIL) {
@@ -122,12 +127,13 @@ __global__ void __launch_bounds__(kNlmThreads) nlm_kernel(const NlmParams Q) {
             const float d = ((d2.x + d2.y) + (d3.x + d3.y)) + dt;
             const float w = exp2f(-d * Q.k2);
             theta += w;
-            const unsigned long long ww = pk(make_float2(w, w));
+            unsigned long long ww;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(ww) : "f"(w));
 #pragma unroll
             for (int u = 0; u < P; ++u) {
 #pragma unroll
                 for (int t = 0; t < NPR; ++t)
-                    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[u][t]) : "l"(ww), "l"(pk(cb[u * pitch + 2 * t])));
+                    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[u][t]) : "l"(ww), "l"(ld2(&cb[u * pitch + 2 * t])));
                 if (TAIL) acct[u] = fmaf(w, cb[u * pitch + PC - 1].x, acct[u]);
             }
         }
