@@ -106,14 +106,20 @@ __device__ __forceinline__ unsigned long long f2_bits(float2 v) {
 
 // (X_r - X_j)^2 summed over the patch (the reference's rows at
 // ref + u * pitch): elements two at a time with packed FP32 subtract and
-// fused multiply-add, even and odd elements in two running sums.
-__device__ __forceinline__ float direct_f32(const PairSrc& X, int p, int C, const float2* ref,
+// fused multiply-add, even and odd elements in two running sums.  FP, FC:
+// the patch side and channels when fixed at compile time (0: runtime p, C),
+// which unrolls the sum completely.
+template <int FP = 0, int FC = 0>
+__device__ __forceinline__ float direct_f32(const PairSrc& X, int p_rt, int C_rt, const float2* ref,
                                             int yc, int xc) {
+    const int p = FP ? FP : p_rt, C = FC ? FC : C_rt;
     const int pc = p * C, np = pc >> 1;
     unsigned long long acc = 0ull;
     float tail = 0.f;
+    const float2* cbase = X.at(yc, xc);
+#pragma unroll
     for (int u = 0; u < p; ++u) {
-        const float2* crow = X.at(yc + u, xc);
+        const float2* crow = cbase + u * X.pitch;
         const float2* rrow = ref + u * X.pitch;
 #pragma unroll 4
         for (int t = 0; t < np; ++t) {
@@ -290,7 +296,7 @@ struct PoolRegs {
 // the patches of its window, N (C = 1) every norm of its window.  Returns
 // true on overflow: nothing is written and U is the (K+1)-th smallest key of
 // the pool's direct distances (the window is recomputed).
-template <int S, class Src, class T>
+template <int S, class Src, class T, int FP = 0, int FC = 0>
 __device__ bool rerank_ref(const RerankParams& P, const RerankJob& J, const Src& X, const PlainSrc& N,
                            int ry, int rx, int lane, const PoolRegs<S>& pool, unsigned long long& U) {
     const size_t r = (size_t)ry * J.n_rx + rx;
@@ -357,7 +363,9 @@ __device__ bool rerank_ref(const RerankParams& P, const RerankJob& J, const Src&
     for (int i = 0; i < S; ++i) {
         key[i] = kNone;
         if (member[i]) {
-            const float d32 = direct_f32(X, P.p, P.C, ref, yc[i], xc[i]);
+            float d32;
+            if constexpr (sizeof(T) == sizeof(float2)) d32 = direct_f32<FP, FC>(X, P.p, P.C, ref, yc[i], xc[i]);
+            else d32 = direct_f32(X, P.p, P.C, ref, yc[i], xc[i]);
             key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)pool.off[i];
             // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
             const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
@@ -489,7 +497,8 @@ __device__ __forceinline__ int tile_job(const RerankParams& P, int t) {
     return lo;
 }
 
-template <int S>
+// FP, FC: patch side and channels fixed at compile time (0: from P).
+template <int S, int FP, int FC>
 __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
     extern __shared__ __align__(16) float2 sm2[];
     __shared__ unsigned long long list_s[kFbSlots * 32];  // overflow: window keys, then a list
@@ -545,7 +554,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
         }
         if (i + kTileWarps < nref) pool.load(P, J, (size_t)(ry0 + qi) * J.n_rx + rx0 + ri, lane);
         unsigned long long U;
-        if (rerank_ref<S, PairSrc, float2>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
+        if (rerank_ref<S, PairSrc, float2, FP, FC>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
             const int o = atomicAdd(&ovf_n, 1);
             ovf_ref[o] = i;
             ovf_u[o] = U;
@@ -624,9 +633,12 @@ bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
 
 template <int S>
 cudaError_t launch_s(const RerankParams& P, bool tiled, int smem, int grid, cudaStream_t st) {
-    if (tiled) {
-        cudaFuncSetAttribute(rerank_tile_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        rerank_tile_kernel<S><<<grid, kTileWarps * 32, smem, st>>>(P);
+    if (tiled && P.p == 8 && P.C == 1) {  // the 8 x 8 grey patch, unrolled
+        cudaFuncSetAttribute(rerank_tile_kernel<S, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        rerank_tile_kernel<S, 8, 1><<<grid, kTileWarps * 32, smem, st>>>(P);
+    } else if (tiled) {
+        cudaFuncSetAttribute(rerank_tile_kernel<S, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        rerank_tile_kernel<S, 0, 0><<<grid, kTileWarps * 32, smem, st>>>(P);
     } else {
         rerank_global_kernel<S><<<grid, 128, 0, st>>>(P);
     }
