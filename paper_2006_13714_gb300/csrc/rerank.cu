@@ -168,13 +168,16 @@ __device__ __forceinline__ double direct_f64(const Src& X, int p, int C, const T
 }
 
 // rank[i] = number of keys (over all 32*S lane-strided slots) smaller than key[i].
+// Empty slots (kNone) are never smaller than a key, so each slot's scan stops
+// at its last lane that holds one.
 template <int S>
 __device__ __forceinline__ void warp_rank(const unsigned long long (&key)[S], int (&rank)[S]) {
 #pragma unroll
     for (int i = 0; i < S; ++i) rank[i] = 0;
 #pragma unroll
     for (int slot = 0; slot < S; ++slot) {
-        for (int src = 0; src < 32; ++src) {
+        const int nsrc = 32 - __clz((int)__ballot_sync(0xffffffffu, key[slot] != kNone));
+        for (int src = 0; src < nsrc; ++src) {
             const unsigned long long km = __shfl_sync(0xffffffffu, key[slot], src);
 #pragma unroll
             for (int i = 0; i < S; ++i) rank[i] += km < key[i] ? 1 : 0;
