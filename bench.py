@@ -62,6 +62,23 @@ def useful_pairs(H, W, p, win, s):
     return int(cy.sum()) * int(cx.sum())
 
 
+def tc_issued_flop_per_image(H, W, p, win, s, ty=16, tx=8, products=3):
+    """Tensor-core FLOP the tc kernel issues per float32 grey image, for a
+    tile of ty x tx references (the tile the library picks for the 512^2,
+    p 8, s 3, window 39 class): per tile, every candidate column of the
+    window union gets products x p*p/16 K-steps plus the norm step, each an
+    MMA of 128 references x Rb candidate rows x 16 (Rb = the union's rows
+    plus p - 1, rounded up to 16)."""
+    h = (win - 1) // 2
+    ny, nx = (H - p) // s + 1, (W - p) // s + 1
+    rows = (ty - 1) * s + 2 * h + 1
+    cols = (tx - 1) * s + 2 * h + 1
+    Rb = (rows + p - 1 + 15) // 16 * 16
+    tiles = -(-ny // ty) * -(-nx // tx)
+    mmas_per_col = products * (p * p // 16) + 1
+    return float(tiles * cols * mmas_per_col * 2 * 128 * Rb * 16)
+
+
 # ---------------------------------------------------------------- distributed
 
 def dist_setup(args):
@@ -597,6 +614,7 @@ def run_ours(args, world, rank, local, dist):
     tc_ms = tc["ms"] / n_tc
     flop_per_launch = 2.0 * macs_per_image * imgs_per_launch
     achieved = flop_per_launch / (tc_ms / 1e3) / 1e12  # algorithmic TFLOP/s per launch
+    issued_per_launch = tc_issued_flop_per_image(H, W, p, win, s) * imgs_per_launch
     peak = peaks.get("bf16_tflops_sustained")
     peak_src = "of measured (bf16 sustained)"
     if peak is None:
@@ -682,6 +700,8 @@ def run_ours(args, world, rank, local, dist):
                      "frac": achieved / peak, "traffic": traffic, "kernel": "tc_match_kernel",
                      "peak_source": peak_src, "tc_ms_per_launch": tc_ms,
                      "algorithmic_flop_per_launch": flop_per_launch,
+                     "issued_flop_per_launch": issued_per_launch,
+                     "issued_frac": issued_per_launch / (tc_ms / 1e3) / 1e12 / peak,
                      "images_per_launch": imgs_per_launch},
         "cpu_baseline": cpu,
         "gpu_launches": int(round(launches_per_step * args.steps)),
