@@ -206,9 +206,13 @@ int bm_set_algo(bm_ctx* ctx, bm_algo algo);
 int bm_submit(bm_ctx* ctx, const bm_request* req, uint64_t* ticket);
 
 /*
- * Non-blocking completion check.  *done = 1 once the request finished;
- * *status then holds its bm_status.  A ticket is released by the first
- * poll that reports done.  Unknown ticket: BM_ERR_NOT_FOUND.
+ * Non-blocking completion check (never waits for the serving thread's
+ * launches).  *done = 1 once the request finished; *status then holds its
+ * bm_status: BM_OK, BM_ERR_TIMEOUT when a bounded device wait of its
+ * tensor-core kernel ran out (its outputs are incomplete; the wait site is
+ * in bm_last_error of the polling thread), BM_ERR_OOM or BM_ERR_CUDA.  A
+ * ticket is released by the first poll that reports done.  Unknown ticket:
+ * BM_ERR_NOT_FOUND.
  */
 int bm_poll(bm_ctx* ctx, uint64_t ticket, int* done, int* status);
 
@@ -348,7 +352,12 @@ int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, in
  * cudaMalloc, cudaFree or other allocating routine: every intermediate
  * buffer (bf16 operand planes, patch norms, float32 candidate pool, status
  * word, counters) is carved from one array in device memory of
- * BM_STATIC_SCRATCH_BYTES (16 MiB), reserved with the library's module.
+ * BM_STATIC_SCRATCH_BYTES (16 MiB).  The array belongs to a module of the
+ * library that CUDA loads lazily (its default): the first symbol lookup on a
+ * device reserves it -- bm_static_init(), or else the first bm_match_static
+ * call there -- and that first step can fail when device memory is already
+ * full.  Call bm_static_init() at start-up (or run with
+ * CUDA_MODULE_LOADING=EAGER) to reserve it before memory fills up.
  *
  * Same arguments, conventions, validation and results as bm_match with the
  * default algorithm (device pointers; asynchronous on `stream`).  A job
@@ -369,6 +378,28 @@ int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, in
  * results: order them on one stream, or with events.
  */
 #define BM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Reserves the static array (and the fault word below) on the current
+ * device and looks up their addresses; later calls there do nothing.
+ * Returns BM_OK or BM_ERR_CUDA (module load or lookup failed, e.g. device
+ * memory is full).  Host only; no stream work. */
+int bm_static_init(void);
+
+/* Timeout report of bm_match_static on the current device.  A bounded
+ * device wait of the tensor-core kernel (2 s per wait) that runs out leaves
+ * that call's outputs incomplete; the kernel records the wait site in a
+ * sticky per-device word, which the calls never clear.  bm_static_check
+ * synchronises `stream`, reads the word into a host int and clears it:
+ * BM_OK (no timeout since the last check) or BM_ERR_TIMEOUT with the site in
+ * bm_last_error(NULL).  It allocates nothing.  Check after the calls whose
+ * results you use, on the stream they ran on. */
+int bm_static_check(bm_stream stream);
+
+/* Test hook: mode 1 makes the next bm_match_static call's tensor-core kernel
+ * withhold its first stage once, so that a bounded wait runs out and the
+ * timeout path above is taken (no GPU fault: the kernel returns normally).
+ * 0 cancels.  BM_ERR_INVALID for any other mode. */
+int bm_static_set_fault_injection(int mode);
 
 /* Scratch bytes bm_match_static needs for this job (0 if the arguments are
  * invalid or unsupported).  Host only. */

@@ -89,6 +89,9 @@ def load(build_if_missing: bool = True):
             "bm_get_timing": ([vp, ctypes.POINTER(bm_timing), ci], ci),
             "bm_static_scratch_bytes": ([ci, ci, ci, ci, ci, ci, ci, ci], sz),
             "bm_match_static": ([vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
+            "bm_static_init": ([], ci),
+            "bm_static_check": ([vp], ci),
+            "bm_static_set_fault_injection": ([ci], ci),
             "bm_gather_groups": ([vp, vp, ci, ci, ci, ci, ci, vp, ci, ci, ci, vp, vp], ci),
             "bm_aggregate": ([vp, vp, vp, vp, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_nlm": ([vp, vp, ci, ci, ci, ci, ci, ci, ci, ctypes.c_float, vp, vp, vp], ci),
@@ -153,6 +156,18 @@ def bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx, out_
     """No-allocation matcher (fixed device scratch shared by all calls; see bm.h)."""
     return load().bm_match_static(img, H, W, C, dtype, patch, window, stride, K, out_idx,
                                   out_dist, stream)
+
+
+def bm_static_init() -> int:
+    return load().bm_static_init()
+
+
+def bm_static_check(stream) -> int:
+    return load().bm_static_check(stream)
+
+
+def bm_static_set_fault_injection(mode) -> int:
+    return load().bm_static_set_fault_injection(mode)
 
 
 def bm_gather_groups(ctx, img, H, W, C, dtype, patch, idx, n_ry, n_rx, K, out_groups,

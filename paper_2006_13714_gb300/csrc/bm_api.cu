@@ -78,6 +78,20 @@ int set_error(int code, const char* msg) {
     t_last_error = msg;
     return code;
 }
+
+const char* timeout_message(int code) {
+    static const char* const msgs[] = {
+        "a bounded device wait of the tensor-core kernel ran out (unknown site)",
+        "a bounded device wait of the tensor-core kernel ran out (stage free)",
+        "a bounded device wait of the tensor-core kernel ran out (accumulator free)",
+        "a bounded device wait of the tensor-core kernel ran out (stage filled)",
+        "a bounded device wait of the tensor-core kernel ran out (accumulator filled)",
+        "a bounded device wait of the tensor-core kernel ran out (A operand free)",
+        "a bounded device wait of the tensor-core kernel ran out (tile staged)",
+        "a bounded device wait of the tensor-core kernel ran out (A operand formed)"};
+    const int site = code - 0x100;
+    return msgs[site >= 1 && site <= 7 ? site : 0];
+}
 }  // namespace bm
 
 namespace {
@@ -98,6 +112,7 @@ struct GraphEntry {
 struct Batch {
     cudaEvent_t ev;
     int slot;
+    int ring;  // status ring entry: per-job error words (device) and their host copy
     size_t bytes;
     std::vector<uint64_t> ids;
 };
@@ -105,6 +120,7 @@ struct Batch {
 struct Ticket {
     bm_request req;
     int status = BM_OK;
+    std::string msg;  // bm_last_error text of a failed request (set at retire)
     bool admitted = false;
     bool done = false;
     size_t ws_bytes = 0;
@@ -170,8 +186,15 @@ struct bm_ctx {
     // serving
     static constexpr int kSlots = 4;
     static constexpr int kMaxBatch = 64;  // requests per admitted batch
+    static constexpr int kRing = 2 * kSlots;  // batches in flight at most
     cudaStream_t slot_stream[kSlots] = {};
     int slot_busy[kSlots] = {};
+    // per-job error words of the batches in flight: entry r holds kMaxBatch
+    // words on the device and their pinned host copy (read at retire)
+    int* d_ring = nullptr;
+    int* h_ring = nullptr;
+    bool ring_busy[kRing] = {};
+    cudaStream_t aux_stream = nullptr;  // reads of the fault word and counters
     std::mutex q_mu;
     std::condition_variable q_cv;
     std::deque<uint64_t> pending;
@@ -427,9 +450,11 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
 // direct jobs, then the preparation kernels of the tensor-core jobs (one
 // launch per stage), their cross term + top-K (persistent launches, one per
 // class), and the float32 re-ranks (one launch per class).  count: add the
-// jobs to the context counters.
+// jobs to the context counters.  job_status (nullable, device): job i's
+// tensor-core kernel writes its timeout code to job_status[i] (the caller
+// zeroes the words).
 int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, void* ws,
-                  const size_t* offs, cudaStream_t st, bool count) {
+                  const size_t* offs, cudaStream_t st, bool count, int* job_status = nullptr) {
     std::vector<int> tc_ids;
     std::vector<TcArgs> args(n);
     std::vector<PrepJob> pjs;
@@ -441,6 +466,7 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
             PrepJob pj;
             job_views(gs[i], reqs[i], static_cast<char*>(ws) + offs[i], pj, args[i]);
             args[i].fault = ctx->d_fault;
+            if (job_status) args[i].status = job_status + i;
             pjs.push_back(pj);
             tc_ids.push_back(i);
         }
@@ -459,6 +485,11 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
             tg.push_back(gs[i]);
             ta.push_back(args[i]);
         }
+        // the fault-injection test hook applies to the first tensor-core launch
+        // (never inside a graph capture: every replay would repeat it)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (cap == cudaStreamCaptureStatusNone) ta[0].inject = ctx->inject.exchange(0);
         const std::vector<int> ch = tc_choices(ctx, tg.data(), ta.data(), (int)tg.size(), st);
         int nl = 0;
         cudaError_t e = timed(ctx, BM_STAGE_TC, st, [&] {
@@ -529,20 +560,19 @@ namespace {
 
 // Reads and clears the context's sticky timeout word (the caller has
 // synchronised the work it wants covered): BM_ERR_TIMEOUT naming the wait
-// site if a bounded device wait of the tensor-core kernel ran out.
+// site if a bounded device wait of the tensor-core kernel ran out.  The copy
+// runs on the context's own non-blocking stream, so other streams keep
+// running meanwhile.
 int take_fault(bm_ctx* ctx) {
     int v = 0;
-    cudaError_t e = cudaMemcpy(&v, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(&v, ctx->d_fault, sizeof(int), cudaMemcpyDeviceToHost, ctx->aux_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux_stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device fault word");
     if (v == 0) return BM_OK;
-    if ((e = cudaMemset(ctx->d_fault, 0, sizeof(int))) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ctx->d_fault, 0, sizeof(int), ctx->aux_stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->aux_stream)) != cudaSuccess)
         return cuda_fail(e, "clearing the device fault word");
-    static const char* const sites[] = {"?", "stage free", "accumulator free", "stage filled",
-                                        "accumulator filled", "A operand free", "tile staged",
-                                        "A operand formed"};
-    const int site = v - 0x100;
-    return fail(BM_ERR_TIMEOUT, std::string("a bounded device wait of the tensor-core kernel ran out (") +
-                                    (site >= 1 && site <= 7 ? sites[site] : "unknown site") + ")");
+    return fail(BM_ERR_TIMEOUT, timeout_message(v));
 }
 
 }  // namespace
@@ -593,7 +623,9 @@ void worker_loop(bm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     std::unique_lock<std::mutex> lk(ctx->q_mu);
     while (true) {
-        // 1. retire finished batches
+        // 1. retire finished batches: a job whose tensor-core kernel ran out of
+        // a bounded wait (its error word, copied to the host ring entry after
+        // the batch's kernels) fails with BM_ERR_TIMEOUT
         for (size_t bi = 0; bi < ctx->batches.size();) {
             Batch& b = ctx->batches[bi];
             cudaError_t q = cudaEventQuery(b.ev);
@@ -601,28 +633,37 @@ void worker_loop(bm_ctx* ctx) {
                 ++bi;
                 continue;
             }
-            for (uint64_t id : b.ids) {
-                Ticket& t = ctx->tickets[id];
+            const int* words = ctx->h_ring + (size_t)b.ring * bm_ctx::kMaxBatch;
+            for (size_t i = 0; i < b.ids.size(); ++i) {
+                Ticket& t = ctx->tickets[b.ids[i]];
                 if (q != cudaSuccess && t.status == BM_OK) {
-                    t_last_error = std::string("request failed: ") + cudaGetErrorString(q);
+                    t.msg = std::string("request failed: ") + cudaGetErrorString(q);
                     t.status = BM_ERR_CUDA;
+                } else if (q == cudaSuccess && words[i] != 0 && t.status == BM_OK) {
+                    t.msg = timeout_message(words[i]);
+                    t.status = BM_ERR_TIMEOUT;
                 }
                 t.done = true;
             }
             cudaEventDestroy(b.ev);
             ctx->used -= b.bytes;
             ctx->slot_busy[b.slot] -= 1;
+            ctx->ring_busy[b.ring] = false;
             ctx->batches.erase(ctx->batches.begin() + bi);
         }
         // 2. continuous batching: the pending requests that fit the memory
         // budget (in arrival order) are admitted together as one batch on the
         // least busy stream -- one persistent launch per kernel stage -- as
-        // soon as a stream slot is free
+        // soon as a stream slot is free.  The queue lock is released while the
+        // batch is enqueued, so bm_submit and bm_poll never wait for launches.
         while (!ctx->pending.empty()) {
             int slot = 0;
             for (int s = 1; s < bm_ctx::kSlots; ++s)
                 if (ctx->slot_busy[s] < ctx->slot_busy[slot]) slot = s;
             if (ctx->slot_busy[slot] >= 2) break;  // every stream already has two batches in flight
+            int ring = 0;
+            while (ring < bm_ctx::kRing && ctx->ring_busy[ring]) ++ring;
+            if (ring == bm_ctx::kRing) break;
             std::vector<uint64_t> ids;
             size_t batch_bytes = 0;
             while (!ctx->pending.empty() && ids.size() < (size_t)bm_ctx::kMaxBatch) {
@@ -642,6 +683,8 @@ void worker_loop(bm_ctx* ctx) {
             size_t off = 0;
             for (int i = 0; i < n; ++i) {
                 Ticket& t = ctx->tickets[ids[i]];
+                t.admitted = true;
+                t.slot = slot;
                 reqs[i] = t.req;
                 validate(t.req, gs[i]);
                 offs[i] = off;
@@ -649,22 +692,35 @@ void worker_loop(bm_ctx* ctx) {
             }
             ctx->used += batch_bytes;
             ctx->slot_busy[slot] += 1;
+            ctx->ring_busy[ring] = true;
+            lk.unlock();
+            // enqueue without the lock (this thread alone uses the slot streams)
+            int* words = ctx->d_ring + (size_t)ring * bm_ctx::kMaxBatch;
+            int* hwords = ctx->h_ring + (size_t)ring * bm_ctx::kMaxBatch;
+            std::memset(hwords, 0, sizeof(int) * bm_ctx::kMaxBatch);
             void* ws = nullptr;
-            cudaError_t e = cudaSuccess;
-            if (batch_bytes) e = cudaMallocAsync(&ws, batch_bytes, st);
-            const int rc = e == cudaSuccess
-                               ? enqueue_batch(ctx, gs.data(), reqs.data(), n, ws, offs.data(), st, true)
-                               : BM_ERR_OOM;
+            cudaError_t e = cudaMemsetAsync(words, 0, sizeof(int) * n, st);
+            if (e == cudaSuccess && batch_bytes) e = cudaMallocAsync(&ws, batch_bytes, st);
+            std::string err;
+            int rc = BM_ERR_OOM;
+            if (e == cudaSuccess) {
+                rc = enqueue_batch(ctx, gs.data(), reqs.data(), n, ws, offs.data(), st, true, words);
+                if (rc != BM_OK) err = t_last_error;
+            } else {
+                err = std::string("batch workspace: ") + cudaGetErrorString(e);
+                cudaGetLastError();
+            }
             if (ws) cudaFreeAsync(ws, st);
+            cudaMemcpyAsync(hwords, words, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
             cudaEvent_t ev = nullptr;
             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
             cudaEventRecord(ev, st);
-            ctx->batches.push_back(Batch{ev, slot, batch_bytes, ids});
+            lk.lock();
+            ctx->batches.push_back(Batch{ev, slot, ring, batch_bytes, ids});
             for (int i = 0; i < n; ++i) {
                 Ticket& t = ctx->tickets[ids[i]];
-                t.slot = slot;
-                t.admitted = true;
                 t.status = rc;
+                if (rc != BM_OK) t.msg = err;
             }
         }
         if (ctx->stop) {
@@ -713,7 +769,11 @@ int bm_create(bm_ctx** out, int device, size_t mem_budget_bytes, const char* tun
         (e = cudaMemset(ctx->d_fault, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->d_ring, sizeof(int) * bm_ctx::kRing * bm_ctx::kMaxBatch)) != cudaSuccess ||
+        (e = cudaHostAlloc(&ctx->h_ring, sizeof(int) * bm_ctx::kRing * bm_ctx::kMaxBatch,
+                           cudaHostAllocDefault)) != cudaSuccess) {
         delete ctx;
         return cuda_fail(e, "context setup");
     }
@@ -748,6 +808,9 @@ void bm_destroy(bm_ctx* ctx) {
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_fault) cudaFree(ctx->d_fault);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->d_ring) cudaFree(ctx->d_ring);
+    if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
     for (int b = 0; b < 2; ++b) {
         if (ctx->hb_buf[b]) cudaFree(ctx->hb_buf[b]);
         if (ctx->hb_stream[b]) cudaStreamDestroy(ctx->hb_stream[b]);
@@ -1026,6 +1089,8 @@ int bm_poll(bm_ctx* ctx, uint64_t ticket, int* done, int* status) {
     if (it == ctx->tickets.end()) return fail(BM_ERR_NOT_FOUND, "unknown ticket");
     *done = it->second.done ? 1 : 0;
     *status = it->second.status;
+    // a failed request's message becomes the polling thread's bm_last_error
+    if (it->second.done && it->second.status != BM_OK) t_last_error = it->second.msg;
     if (it->second.done) ctx->tickets.erase(it);
     return BM_OK;
 }
@@ -1034,7 +1099,8 @@ int bm_get_stats(bm_ctx* ctx, bm_stats* out) {
     if (!ctx || !out) return fail(BM_ERR_INVALID, "null argument");
     DeviceGuard dg(ctx->device);
     unsigned long long c[4] = {0, 0, 0, 0};
-    cudaError_t e = cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost, ctx->aux_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux_stream);
     if (e != cudaSuccess) return cuda_fail(e, "counter read");
     out->matches = ctx->matches.load();
     out->refs = ctx->refs.load();

@@ -191,6 +191,9 @@ cudaError_t launch_rerank_batch(const Geom* gs, const RerankArgs* as, int n,
 
 // Sets the calling thread's bm_last_error message and returns code.
 int set_error(int code, const char* msg);
+// Text of a timeout code (0x100 + wait site) written by the tensor-core
+// kernel's abort path; static storage.
+const char* timeout_message(int code);
 
 // (f1) patch groups and reconstruction (groups.cu).
 // groups[pt][u][v*C + c] = img[y + u][x + v][c] for idx[pt] = y*W + x (pt =

@@ -5,9 +5,16 @@
 // latency-bound loop), and in a process whose device memory is already held
 // by another allocator a fresh allocation can fail part-way through a run.
 // Every intermediate buffer of the tensor-core path comes from one fixed
-// array in device memory, reserved when the library's module is loaded.  The
-// kernels are the ones bm_match runs, on the same geometry, so the results
-// are the same.
+// array in device memory.  The array belongs to this file's module: CUDA
+// loads modules lazily by default, so the array is reserved by the first
+// symbol lookup on a device (bm_static_init, or the first bm_match_static
+// there), or at start-up under CUDA_MODULE_LOADING=EAGER.  The kernels are
+// the ones bm_match runs, on the same geometry, so the results are the same.
+//
+// Timeouts: a bounded device wait of the tensor-core kernel that runs out
+// leaves the job's outputs incomplete.  The kernel then records its code in
+// a sticky per-device fault word (outside the part each call clears), which
+// bm_static_check reads and clears.
 //
 // Limits and sharing: the array holds BM_STATIC_SCRATCH_BYTES; larger jobs
 // are rejected with BM_ERR_TOO_LARGE before anything is launched.  All calls
@@ -16,6 +23,7 @@
 #include "bm_internal.h"
 
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -24,10 +32,14 @@ namespace {
 
 // The scratch array.  One copy per device, reserved at module load.
 static __device__ __align__(256) unsigned char g_scratch[BM_STATIC_SCRATCH_BYTES];
+// Sticky timeout word: the first timeout code since the last bm_static_check.
+static __device__ int g_fault;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_base[kMaxDevices] = {};
+int* g_fault_ptr[kMaxDevices] = {};
+std::atomic<int> g_inject{0};  // test hook: the next call's kernel withholds its first stage
 
 size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -72,9 +84,9 @@ int check_args(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, i
     return rc;
 }
 
-// Device address of the array on the current device; the first call per
-// device looks it up.
-int scratch_base(void** out) {
+// Device addresses of the array and of the fault word on the current
+// device; the first call per device looks them up (which loads the module).
+int scratch_base(void** out, int** fault) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
@@ -83,13 +95,17 @@ int scratch_base(void** out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_base[dev]) {
         void* ptr = nullptr;
+        void* fptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_scratch);
-        if (e != cudaSuccess || !ptr)
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&fptr, g_fault);
+        if (e != cudaSuccess || !ptr || !fptr)
             return set_error(BM_ERR_CUDA,
                              (std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)).c_str());
         g_base[dev] = ptr;
+        g_fault_ptr[dev] = static_cast<int*>(fptr);
     }
     *out = g_base[dev];
+    if (fault) *fault = g_fault_ptr[dev];
     return BM_OK;
 }
 
@@ -126,7 +142,8 @@ extern "C" int bm_match_static(const void* img, int H, int W, int C, bm_dtype dt
         return set_error(BM_ERR_TOO_LARGE, buf);
     }
     void* base = nullptr;
-    if ((rc = scratch_base(&base)) != BM_OK) return rc;
+    int* fault = nullptr;
+    if ((rc = scratch_base(&base, &fault)) != BM_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* b = static_cast<char*>(base);
     cudaError_t e;
@@ -155,6 +172,8 @@ extern "C" int bm_match_static(const void* img, int H, int W, int C, bm_dtype dt
     a.nrm = nrm;
     a.nsp = nsp;
     a.status = reinterpret_cast<int*>(b);
+    a.fault = fault;
+    a.inject = g_inject.exchange(0);
     if (g.dtype == kU8) {
         a.out_idx = out_idx;
         a.out_dist = static_cast<int32_t*>(out_dist);
@@ -169,5 +188,34 @@ extern "C" int bm_match_static(const void* img, int H, int W, int C, bm_dtype dt
                           counters, st);
         if (e != cudaSuccess) return launch_fail(e, "re-rank kernel launch");
     }
+    return BM_OK;
+}
+
+extern "C" int bm_static_init(void) {
+    void* base = nullptr;
+    return scratch_base(&base, nullptr);
+}
+
+extern "C" int bm_static_check(bm_stream stream) {
+    void* base = nullptr;
+    int* fault = nullptr;
+    int rc = scratch_base(&base, &fault);
+    if (rc != BM_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int v = 0;  // a host int: nothing is allocated
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, fault, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return launch_fail(e, "reading the static fault word");
+    if (v == 0) return BM_OK;
+    if ((e = cudaMemsetAsync(fault, 0, sizeof(int), st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return launch_fail(e, "clearing the static fault word");
+    return set_error(BM_ERR_TIMEOUT, timeout_message(v));
+}
+
+extern "C" int bm_static_set_fault_injection(int mode) {
+    if (mode != 0 && mode != 1) return set_error(BM_ERR_INVALID, "unknown fault injection mode");
+    g_inject.store(mode);
     return BM_OK;
 }

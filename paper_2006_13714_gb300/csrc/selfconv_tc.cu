@@ -97,6 +97,7 @@ struct TcJob {
     int32_t* out_dist;        // uint8: final distances
     int32_t* pool_idx;        // float32: pool
     float* pool_score;
+    int* status;              // nullable: the job's error word (timeout code on abort)
     int H, W, n_ry, n_rx, Hc, Wc;
     int tiles_x, tile_begin;  // tiles along x; index of the job's first tile
 };
@@ -106,11 +107,11 @@ constexpr int kMaxJobs = 64;  // jobs per launch (kept inline in the kernel para
 struct TcParams {
     TcGeom g;
     int njobs, total_tiles;
-    int* status;
     int* fault;   // nullable: sticky copy of the first timeout code (context-wide)
     int inject;   // test hook: CTA 0's first producer skips publishing its first stage
     TcJob jobs[kMaxJobs];
 };
+static_assert(sizeof(TcParams) <= 32764, "kernel parameters exceed the 32 KB limit");
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -1109,8 +1110,11 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
+    // an aborted CTA leaves parts of any job of the launch unwritten: every
+    // job's error word gets the timeout code
     if (threadIdx.x == 0 && *abort_flag) {
-        atomicExch(P.status, 0x100 + *abort_flag);
+        for (int j = 0; j < P.njobs; ++j)
+            if (P.jobs[j].status) atomicExch(P.jobs[j].status, 0x100 + *abort_flag);
         if (P.fault) atomicCAS(P.fault, 0, 0x100 + *abort_flag);
     }
 }
@@ -1268,6 +1272,7 @@ bool make_job(TcJob& j, const Geom& g, const TcGeom& t, const TcArgs& a, int til
     j.H = g.H; j.W = g.W; j.n_ry = g.n_ry; j.n_rx = g.n_rx; j.Hc = g.Hc; j.Wc = g.Wc;
     j.tiles_x = (g.n_rx + t.tx - 1) / t.tx;
     j.tile_begin = tile_begin;
+    j.status = a.status;
     return true;
 }
 
@@ -1336,7 +1341,6 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         P = TcParams{};
         const int choice = choices ? choices[i] : -1;
         if (!make_tc_geom(gs[i], P.g, choice)) return cudaErrorNotSupported;
-        P.status = as[i].status;
         P.fault = as[i].fault;
         P.inject = as[i].inject;
         int tiles = 0, nj = 0;

@@ -49,3 +49,48 @@ def test_invalid_injection_mode():
     with B.Context(0) as ctx:
         assert B.bm_set_fault_injection(ctx.handle, 7) == B.BM_ERR_INVALID
         assert B.bm_check(None, None) == B.BM_ERR_INVALID
+
+
+def _wait_done(ctx, ticket, limit_s=60.0):
+    import time
+    t0 = time.time()
+    while True:
+        done, status = ctx.poll(ticket)
+        if done:
+            return status
+        assert time.time() - t0 < limit_s, "served request did not finish"
+        time.sleep(0.002)
+
+
+def test_served_request_reports_timeout():
+    """A served request whose kernel ran out of a bounded wait is not BM_OK.
+
+    The serving thread copies every job's error word to the host after the
+    batch and fails the ticket with BM_ERR_TIMEOUT; the poll that reports it
+    sets the polling thread's bm_last_error to the wait site.  The next
+    request on the same context is served correctly.
+    """
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    img = synth.gray(64, 64, 25.0, 322, np.uint8)
+    t = torch.from_numpy(img).cuda()
+    with B.Context(0) as ctx:
+        idx, dist = ctx.outputs(t, 8, 1, 16)
+        torch.cuda.synchronize()
+        assert B.bm_set_fault_injection(ctx.handle, 1) == B.BM_OK
+        tk = ctx.submit(B.Context.request(t, 8, 21, 1, 16, idx, dist))
+        status = _wait_done(ctx, tk)
+        assert status == B.BM_ERR_TIMEOUT, status
+        msg = B.bm_last_error(ctx.handle)
+        assert "ran out" in msg, msg
+        # the context-wide sticky word saw it too; bm_check clears it
+        st = torch.cuda.current_stream()
+        assert B.bm_check(ctx.handle, st.cuda_stream) == B.BM_ERR_TIMEOUT
+        assert B.bm_check(ctx.handle, st.cuda_stream) == B.BM_OK
+        idx2, dist2 = ctx.outputs(t, 8, 1, 16)
+        torch.cuda.synchronize()
+        tk2 = ctx.submit(B.Context.request(t, 8, 21, 1, 16, idx2, dist2))
+        assert _wait_done(ctx, tk2) == B.BM_OK
+        oi, od = O.match(img, 8, 21, 1, 16)
+        assert np.array_equal(idx2.cpu().numpy(), oi)
+        assert np.array_equal(dist2.cpu().numpy().astype(np.int64), od)

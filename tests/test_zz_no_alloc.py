@@ -35,6 +35,15 @@ def _agree(idx_a, dist_a, idx_b, dist_b, is_u8):
             assert abs(float(dist_a[r, j]) - kth) <= REL_TOL * max(kth, 1.0)
 
 
+def _static(img, p, win, s, K, idx, dist, stream):
+    H, W = img.shape[0], img.shape[1]
+    C = 1 if img.dim() == 2 else img.shape[2]
+    import torch
+    dt = B.BM_U8 if img.dtype == torch.uint8 else B.BM_F32
+    return B.bm_match_static(img.data_ptr(), H, W, C, dt, p, win, s, K, idx.data_ptr(),
+                             dist.data_ptr(), stream.cuda_stream)
+
+
 def test_scratch_bytes_host_only():
     # 512 x 512 float32, p 8, s 3, window 39, K 16: planes + norms + pool
     n = B.bm_static_scratch_bytes(512, 512, 1, B.BM_F32, 8, 39, 3, 16)
@@ -93,3 +102,90 @@ def test_static_rejects_jobs_beyond_the_scratch():
     assert "too large" in B.bm_last_error()
     torch.cuda.synchronize()
     assert bool((idx == 7).all()) and bool((dist == 7.0).all())
+
+
+def test_direct_path_geometry_needs_only_the_header():
+    # window 127 with K 128 is outside the tensor-core kernel's tiling (its
+    # staged candidate rows exceed one TMA box): only the 256-byte header
+    assert B.bm_static_scratch_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 256
+
+
+@pytest.mark.gpu
+def test_static_allocates_nothing_and_covers_direct_and_four_channels():
+    """After a warm-up call, further calls leave free device memory unchanged.
+
+    Covers a 4-channel uint8 job (tensor cores), a float32 job and a
+    geometry that takes the direct kernel, each compared with bm_match.
+    """
+    import torch
+
+    torch.cuda.set_device(0)
+    assert B.bm_static_init() == B.BM_OK
+    jobs = [
+        (synth.rgbnir(200, 180, 20.0, 7101), 8, 39, 3, 32),            # u8, C 4
+        (synth.gray(256, 240, 25.0, 7102, np.float32), 8, 39, 3, 16),  # f32, C 1
+        (synth.gray(160, 150, 20.0, 7103, np.uint8), 8, 127, 4, 128),  # direct kernel
+    ]
+    assert B.bm_static_scratch_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 256
+    ctx = B.Context(0)
+    st = torch.cuda.current_stream()
+    data = []
+    for img_np, p, win, s, K in jobs:
+        img = torch.from_numpy(np.ascontiguousarray(img_np)).cuda()
+        idx, dist = ctx.outputs(img, p, s, K)
+        data.append((img, idx, dist))
+    torch.cuda.synchronize()
+    # warm-up: loads every kernel module these calls use
+    for (img_np, p, win, s, K), (img, idx, dist) in zip(jobs, data):
+        assert _static(img, p, win, s, K, idx, dist, st) == B.BM_OK, B.bm_last_error()
+    torch.cuda.synchronize()
+    assert B.bm_static_check(st.cuda_stream) == B.BM_OK
+    free0, _ = torch.cuda.mem_get_info()
+    for (img_np, p, win, s, K), (img, idx, dist) in zip(jobs, data):
+        assert _static(img, p, win, s, K, idx, dist, st) == B.BM_OK, B.bm_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert B.bm_static_check(st.cuda_stream) == B.BM_OK
+    for (img_np, p, win, s, K), (img, idx, dist) in zip(jobs, data):
+        ridx, rdist = ctx.match(img, p, win, s, K)
+        torch.cuda.synchronize()
+        _agree(idx.cpu().numpy(), dist.cpu().numpy(), ridx.cpu().numpy(), rdist.cpu().numpy(),
+               img_np.dtype == np.uint8)
+    ctx.close()
+
+
+@pytest.mark.gpu
+def test_static_timeout_is_reported_by_static_check():
+    """A bounded wait that runs out inside bm_match_static is not silent.
+
+    The test hook withholds one stage publication of the next call's
+    tensor-core kernel; its wait runs out (a bounded wait, no GPU fault), the
+    kernel records the site in the sticky static fault word, and
+    bm_static_check returns BM_ERR_TIMEOUT once, then BM_OK.  The next call
+    gives the right result.
+    """
+    import torch
+
+    from oracle import oracle as O
+
+    torch.cuda.set_device(0)
+    img_np = synth.gray(64, 64, 25.0, 7104, np.uint8)
+    img = torch.from_numpy(img_np).cuda()
+    ry, rx = B.bm_num_refs(64, 64, 8, 1)
+    idx = torch.empty((ry * rx, 16), dtype=torch.int32, device="cuda")
+    dist = torch.empty((ry * rx, 16), dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    assert B.bm_static_check(st.cuda_stream) == B.BM_OK
+    assert B.bm_static_set_fault_injection(7) == B.BM_ERR_INVALID
+    assert B.bm_static_set_fault_injection(1) == B.BM_OK
+    assert _static(img, 8, 21, 1, 16, idx, dist, st) == B.BM_OK
+    rc = B.bm_static_check(st.cuda_stream)
+    assert rc == B.BM_ERR_TIMEOUT, rc
+    assert "ran out" in B.bm_last_error()
+    assert B.bm_static_check(st.cuda_stream) == B.BM_OK
+    assert _static(img, 8, 21, 1, 16, idx, dist, st) == B.BM_OK
+    assert B.bm_static_check(st.cuda_stream) == B.BM_OK
+    oi, od = O.match(img_np, 8, 21, 1, 16)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    assert np.array_equal(dist.cpu().numpy().astype(np.int64), od)
