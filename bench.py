@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--images", type=int, default=160, help="512^2 images per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency stream")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests of the serving stream (a seeded prefix of the 2000-request stream)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--minimal", action="store_true",
                     help="timed loop only (no baselines, latency or e2e); for profiler runs")
@@ -252,59 +254,98 @@ def profiled_traffic(images_per_launch):
         return None
 
 
-def serve_latency(ctx, pkg, synth, dev, n=160, seed=SEED_BASE + 55):
-    """Serving: a seeded Poisson stream of mixed requests (shapes of the
-    serving workload: uint8/float32, C in {1, 4}, patch 7/8, window 39/61,
-    K 16/32/70; sides drawn in [128, 768] to bound the run) submitted to the
-    context's queue at their arrival times; per-request latency = completion
-    seen by polling - arrival.  The rate is 0.7 x the serial throughput of a
-    calibration pass (requests matched one after another)."""
+def serve_stream(ctx, pkg, synth, dev, n=2000, seed=SEED_BASE + 55, side=2048):
+    """Serving workload: n seeded requests (uint8 / float32, C 1 or 4, sides
+    uniform in [128, side], patch 8 (stride 3) or 7 (stride 4), window 39 or
+    61, K 16 / 32 / 70) admitted under the context's 40 GB workspace budget,
+    with every input and output resident on the device.  Each request's
+    image is a seeded crop of one of four side x side synthetic base images
+    (one per dtype and channel count), cut on the device.  Three passes over
+    the same requests:
+      serial     bm_match one request at a time (synchronised after each);
+      saturated  every request submitted at once: aggregate ref-patches/s;
+      poisson    submitted at seeded Poisson arrival times at 0.7 x the
+                 serial request rate: latency = completion seen by polling
+                 minus arrival, p50 / p99.
+    """
     import torch
-    draws = synth.serve_requests(n, seed, 1.0)
-    rng = np.random.default_rng(seed)
+    draws = synth.serve_requests(2000, seed, 1.0)[:n]
+    bases = {
+        ("u8", 1): synth.gray(side, side, 20.0, seed + 1, np.uint8),
+        ("f32", 1): synth.gray(side, side, 20.0, seed + 2, np.float32),
+        ("u8", 4): synth.rgbnir(side, side, 20.0, seed + 3),
+        ("f32", 4): synth.rgbnir(side, side, 20.0, seed + 4).astype(np.float32),
+    }
+    dbases = {k: torch.from_numpy(v).to(dev) for k, v in bases.items()}
     jobs = []
+    refs = []
     for d in draws:
-        H = 128 + int(d["H"] - 128) * (768 - 128) // (2048 - 128)
-        W = 128 + int(d["W"] - 128) * (768 - 128) // (2048 - 128)
-        dt = np.uint8 if d["dtype"] == "u8" else np.float32
-        if d["C"] == 1:
-            img = synth.gray(H, W, 20.0, d["seed"], dt)
-        else:
-            img = np.ascontiguousarray(np.stack(
-                [synth.gray(H, W, 20.0, d["seed"] * 4 + c, dt) for c in range(4)], axis=-1))
-        t = torch.from_numpy(img).to(dev)
+        H = min(side, d["H"])
+        W = min(side, d["W"])
+        rng = np.random.default_rng(d["seed"])
+        y0 = int(rng.integers(0, side - H + 1))
+        x0 = int(rng.integers(0, side - W + 1))
+        t = dbases[(d["dtype"], d["C"])][y0:y0 + H, x0:x0 + W].contiguous()
         idx, dist_t = ctx.outputs(t, d["patch"], d["stride"], d["K"])
         req = pkg.Context.request(t, d["patch"], d["window"], d["stride"], d["K"], idx, dist_t)
-        jobs.append((t, idx, dist_t, req))
+        jobs.append((t, idx, dist_t, req, d))
+        ny, nx = pkg.bm_num_refs(H, W, d["patch"], d["stride"])
+        refs.append(ny * nx)
+    del dbases
     torch.cuda.synchronize(dev)
+    total_refs = float(sum(refs))
+    in_bytes = sum(j[0].numel() * j[0].element_size() for j in jobs)
+    out_bytes = sum(j[1].numel() * 4 + j[2].numel() * 4 for j in jobs)
 
-    def wait(ticket):
-        t_end = time.perf_counter() + 120.0
+    def wait(ticket, limit=300.0):
+        t_end = time.perf_counter() + limit
         while True:
             if time.perf_counter() > t_end:
-                raise RuntimeError("serving request did not finish in 120 s")
+                raise RuntimeError("serving request did not finish")
             done, st = ctx.poll(ticket)
             if done:
                 if st != 0:
                     raise pkg.BMError(st, "serving request failed")
                 return
+            time.sleep(0.00005)
 
-    # calibration: serial throughput over a prefix of the stream
+    # warm-up: one request of every class (kernel loads, workspaces)
+    seen = set()
+    for j in jobs:
+        d = j[4]
+        key = (d["dtype"], d["C"], d["patch"], d["window"], d["K"])
+        if key not in seen:
+            seen.add(key)
+            wait(ctx.submit(j[3]))
+    torch.cuda.synchronize(dev)
+
+    # serial: bm_match one request at a time
+    stream = torch.cuda.Stream(dev)
     t0 = time.perf_counter()
-    ncal = 24
-    for j in jobs[:ncal]:
-        wait(ctx.submit(j[3]))
-    serial_rps = ncal / (time.perf_counter() - t0)
+    for t, idx, dist_t, req, d in jobs:
+        ctx.match(t, d["patch"], d["window"], d["stride"], d["K"], out=(idx, dist_t), stream=stream)
+        stream.synchronize()
+    serial_s = time.perf_counter() - t0
+
+    # saturated: everything submitted at once
+    t0 = time.perf_counter()
+    tks = [ctx.submit(j[3]) for j in jobs]
+    for tk in tks:
+        wait(tk)
+    sat_s = time.perf_counter() - t0
+
+    # Poisson arrivals at 0.7 x the serial request rate
+    serial_rps = n / serial_s
     rate = 0.7 * serial_rps
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    arrivals = np.cumsum(np.random.default_rng(seed + 9).exponential(1.0 / rate, size=n))
     lat = [None] * n
     tickets = {}
     start = time.perf_counter()
     i = 0
     while i < n or tickets:
         now = time.perf_counter() - start
-        if now > arrivals[-1] + 120.0:
-            raise RuntimeError("serving stream did not finish in 120 s after the last arrival")
+        if now > arrivals[-1] + 300.0:
+            raise RuntimeError("serving stream did not finish in 300 s after the last arrival")
         while i < n and arrivals[i] <= now:
             tickets[ctx.submit(jobs[i][3])] = i
             i += 1
@@ -315,14 +356,94 @@ def serve_latency(ctx, pkg, synth, dev, n=160, seed=SEED_BASE + 55):
                     raise pkg.BMError(st, "serving request failed")
                 k = tickets.pop(tk)
                 lat[k] = (time.perf_counter() - start) - arrivals[k]
-        time.sleep(0.0001)
+        time.sleep(0.00005)
     wall = time.perf_counter() - start
     lat_ms = np.array(lat) * 1e3
-    return {"requests": n, "rate_req_per_s": rate, "serial_req_per_s": serial_rps,
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "throughput_req_per_s": n / wall,
-            "workload": "Poisson arrivals; u8/f32, C 1/4, patch 7/8, window 39/61, K 16/32/70, "
-                        "sides 128-768 (seeded)"}
+    cls = {}
+    for k, (t, idx, dist_t, req, d) in enumerate(jobs):
+        key = "f32_c4_p8" if (d["dtype"], d["C"], d["patch"]) == ("f32", 4, 8) else "other"
+        cls.setdefault(key, []).append(lat_ms[k])
+    out = {
+        "requests": n, "ref_patches": total_refs,
+        "serial": {"seconds": serial_s, "ref_patches_per_s": total_refs / serial_s,
+                   "req_per_s": serial_rps, "api": "bm_match, synchronised after each"},
+        "saturated": {"seconds": sat_s, "ref_patches_per_s": total_refs / sat_s,
+                      "vs_serial": serial_s / sat_s, "api": "bm_submit all, bm_poll"},
+        "poisson": {"rate_req_per_s": rate, "p50_ms": float(np.percentile(lat_ms, 50)),
+                    "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+                    "seconds": wall, "ref_patches_per_s": total_refs / wall},
+        "p99_ms_by_class": {k: float(np.percentile(v, 99)) for k, v in cls.items()},
+        "resident_bytes": {"inputs": in_bytes, "outputs": out_bytes},
+        "workload": f"{n} seeded requests (prefix of a 2000-request stream): u8/f32, C 1/4, sides U[128,{side}], patch 8 (s 3) / 7 (s 4), "
+                    "window 39/61, K 16/32/70, 40 GB workspace budget; images are seeded crops "
+                    f"of four {side}x{side} synthetic base images",
+    }
+    for j in jobs:
+        del j
+    return out
+
+
+def batch_row(ctx, pkg, dev, nps, p, win, s, K, label, peaks, steps=5, n_direct=None):
+    """Throughput of one batch workload through bm_match_batch (the graph-
+    captured persistent launches): ref-patches/s, useful cross-term TMAC/s
+    (pairs x p*p*C), the tensor-core kernel's share and its algorithmic
+    fraction of the bf16 peak, and the plain FP32 direct kernel on (a prefix
+    of) the same batch."""
+    import torch
+    stream = torch.cuda.Stream(dev)
+    imgs, outs, reqs, nref = [], [], [], []
+    pairs_mac = 0
+    for a in nps:
+        t = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        idx, dist_t = ctx.outputs(t, p, s, K)
+        imgs.append(t)
+        outs.append((idx, dist_t))
+        reqs.append(pkg.Context.request(t, p, win, s, K, idx, dist_t))
+        H, W = a.shape[0], a.shape[1]
+        C = 1 if a.ndim == 2 else a.shape[2]
+        ny, nx = pkg.bm_num_refs(H, W, p, s)
+        nref.append(ny * nx)
+        pairs_mac += useful_pairs(H, W, p, win, s) * p * p * C
+    refs = sum(nref)
+    for _ in range(3):
+        ctx.match_batch(reqs, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.match_batch(reqs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    ctx.timing(reset=True)
+    ctx.set_timing(True)
+    ctx.match_batch(reqs, stream=stream)
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(False)
+    tm = ctx.timing(reset=True)
+    tc = tm["tc"]
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    tc_tflops = 2.0 * pairs_mac / (tc["ms"] / 1e3) / 1e12 if tc["ms"] > 0 else None
+    nd = len(imgs) if n_direct is None else min(n_direct, len(imgs))
+    e0.record(stream)
+    for i in range(nd):
+        ctx.match_direct(imgs[i], p, win, s, K, out=outs[i], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    d_ms = e0.elapsed_time(e1)
+    d_refs = sum(nref[:nd])
+    direct_rate = d_refs / (d_ms / 1e3)
+    return {
+        "workload": label, "images": len(nps), "ms_per_batch": ms,
+        "ref_patches_per_s": refs / (ms / 1e3), "useful_tmac_per_s": pairs_mac / (ms / 1e3) / 1e12,
+        "tc": {"launches": tc["launches"], "ms": tc["ms"], "share": tc["ms"] / max(1e-9, sum(v["ms"] for v in tm.values())),
+               "algorithmic_tflops": tc_tflops,
+               "frac_of_bf16": (tc_tflops / peak) if tc_tflops else None,
+               "peak_source": "of measured (bf16 sustained)" if peaks.get("bf16_tflops_sustained") else "of fallback"},
+        "stage_ms": {k: v["ms"] for k, v in tm.items() if v["launches"]},
+        "direct_fp32_gpu": {"images": nd, "ref_patches_per_s": direct_rate,
+                            "speedup": (refs / (ms / 1e3)) / direct_rate},
+    }
 
 
 def groups_throughput(ctx, imgs, outs, peaks, stream, dev, n=16):
@@ -666,7 +787,17 @@ def run_ours(args, world, rank, local, dist):
     e2e_s = max_over_ranks(dist, e2e_s, dev)
     e2e_value = nR * n_e2e * e2e_steps * world / e2e_s
 
-    serve = serve_latency(ctx, pkg, synth, dev) if not args.no_serve else None
+    cfg3 = batch_row(ctx, pkg, dev, [synth.gray(Hh, Ww, sg, SEED_BASE + 300 + i, np.float32)
+                                     for i, (Hh, Ww, sg) in enumerate(synth.batch_sizes(32, SEED_BASE + 3))],
+                     7, 61, 4, 70, "32 float32 grey images of seeded uneven sizes (256^2 .. 1024^2, "
+                     "sigma 15/25/50), patch 7, stride 4, window 61, K 70", peaks, n_direct=8)
+    rgbnir4 = [synth.rgbnir(1024, 1024, 20.0, SEED_BASE + 400 + i) for i in range(4)]
+    # 16 distinct images: four seeded stacks, each also flipped three ways
+    rgbnir16 = [np.ascontiguousarray(a[::fy, ::fx]) for a in rgbnir4 for fy, fx in ((1, 1), (-1, 1), (1, -1), (-1, -1))]
+    cfg4 = batch_row(ctx, pkg, dev, rgbnir16,
+                     8, 39, 3, 32, "16 uint8 RGB-NIR 1024x1024x4 images, patch 8, stride 3, window 39, K 32",
+                     peaks, n_direct=4)
+    serve = serve_stream(ctx, pkg, synth, dev, n=args.serve_requests) if not args.no_serve else None
     groups = groups_throughput(ctx, imgs, outs, peaks, stream, dev)
     nlm = nlm_throughput(ctx, imgs, stream, dev, pairs)
     ncc = ncc_throughput(ctx, imgs, stream, dev, pairs)
@@ -708,6 +839,8 @@ def run_ours(args, world, rank, local, dist):
         "clocks": clk,
         "stage_ms_share": stage_share,
         "kernel_ms_per_step_with_stage_events": staged_ms,
+        "config3_batch": cfg3,
+        "config4_rgbnir": cfg4,
         "serve": serve,
         "groups": groups,
         "nlm": nlm,

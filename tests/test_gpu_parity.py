@@ -118,6 +118,52 @@ def test_full_size_sampled_parity(ctx, case, algo):
     compare(img, p, win, s, K, gidx, gdist, refs=refs)
 
 
+WHOLE = [
+    # the headline image and one image of the four-channel workload, every
+    # reference compared (the oracle on all host cores)
+    ("cfg2_512_f32_whole", 512, 512, 1, "f32", 8, 39, 3, 16, 2001),
+    ("cfg4_1024x4_u8_whole", 1024, 1024, 4, "u8", 8, 39, 3, 32, 4001),
+]
+
+
+@pytest.mark.parametrize("case", WHOLE, ids=[c[0] for c in WHOLE])
+def test_full_size_whole_image_parity(ctx, case):
+    name, H, W, C, dt, p, win, s, K, seed = case
+    img = make_image(H, W, C, dt, seed=seed, sigma=20.0 if C == 4 else 25.0)
+    gidx, gdist = run(ctx, img, p, win, s, K, "selfconv")
+    compare(img, p, win, s, K, gidx, gdist, threads=0)
+
+
+def test_uneven_batch_of_32_in_one_call(ctx):
+    """The WNNM-shaped batch: 32 float32 images of seeded uneven sizes
+    (256^2 .. 1024^2, sigma 15/25/50), patch 7, stride 4, window 61, K 70,
+    in one bm_match_batch call (graph-captured persistent launches).  Every
+    image equals its own bm_match bit for bit, and a seeded sample of each
+    image's references (with the grid corners and edges) matches the oracle.
+    """
+    p, win, s, K = 7, 61, 4, 70
+    sizes = synth.batch_sizes(32, 3032)
+    imgs, outs, reqs, nps = [], [], [], []
+    for i, (H, W, sigma) in enumerate(sizes):
+        a = synth.gray(H, W, sigma, 3100 + i, np.float32)
+        t = torch.from_numpy(a).cuda()
+        idx, dist = ctx.outputs(t, p, s, K)
+        nps.append(a)
+        imgs.append(t)
+        outs.append((idx, dist))
+        reqs.append(B.Context.request(t, p, win, s, K, idx, dist))
+    stream = torch.cuda.Stream()
+    ctx.match_batch(reqs, stream=stream)
+    torch.cuda.synchronize()
+    for i, (a, t, (idx, dist)) in enumerate(zip(nps, imgs, outs)):
+        ridx, rdist = ctx.match(t, p, win, s, K)
+        torch.cuda.synchronize()
+        assert torch.equal(ridx, idx) and torch.equal(rdist, dist), f"image {i}"
+        ny, nx = B.bm_num_refs(a.shape[0], a.shape[1], p, s)
+        refs = sample_refs(ny, nx, 60, 3200 + i)
+        compare(a, p, win, s, K, idx.cpu().numpy(), dist.cpu().numpy(), refs=refs, threads=0)
+
+
 def test_selfconv_equals_direct_bitwise_on_u8(ctx):
     img = make_image(200, 180, 1, "u8", seed=5)
     a = run(ctx, img, 8, 39, 3, 16, "selfconv")
