@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--images", type=int, default=160, help="512^2 images per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency stream")
-    ap.add_argument("--serve-requests", type=int, default=400,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream (a seeded prefix of the 2000-request stream)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--minimal", action="store_true",
@@ -374,7 +374,7 @@ def serve_stream(ctx, pkg, synth, dev, n=2000, seed=SEED_BASE + 55, side=2048):
                     "seconds": wall, "ref_patches_per_s": total_refs / wall},
         "p99_ms_by_class": {k: float(np.percentile(v, 99)) for k, v in cls.items()},
         "resident_bytes": {"inputs": in_bytes, "outputs": out_bytes},
-        "workload": f"{n} seeded requests (prefix of a 2000-request stream): u8/f32, C 1/4, sides U[128,{side}], patch 8 (s 3) / 7 (s 4), "
+        "workload": f"{n} seeded requests (of the 2000-request stream): u8/f32, C 1/4, sides U[128,{side}], patch 8 (s 3) / 7 (s 4), "
                     "window 39/61, K 16/32/70, 40 GB workspace budget; images are seeded crops "
                     f"of four {side}x{side} synthetic base images",
     }

@@ -3,13 +3,14 @@
 // The comparison baseline: every distance is the explicit sum of squared
 // differences of Eq. equ:bmMetric_app (§III-E), summed over channels (§IV),
 // in FP32 on the CUDA cores -- no Self-Convolution identity, no tensor
-// cores.  One thread per reference patch; a block holds TRy x 32
-// references and stages the union of their search windows in shared
-// memory.  For the common shapes the window row is register-blocked
-// (all 2h+1 candidates of one candidate row accumulate together, so a
-// shared-memory load feeds 2h+1 fused multiply-adds); other shapes use a
-// generic loop.  For uint8 the FP32 sums are exact (all partial sums are
-// integers below 2^24), so results are bit-exact.
+// cores.  One thread per reference patch; a warp holds one row of 32
+// references, a block TRy warps, and the union of their search windows is
+// staged in shared memory (or, when that union is too large, read through
+// L1).  For patch sides 7 and 8, 1 or 4 channels and windows 21, 39 and 61
+// the window row is register-blocked (all 2h+1 candidates of one candidate
+// row accumulate together, so one load feeds 2h+1 fused multiply-adds);
+// other shapes use a generic loop.  For uint8 the FP32 sums are exact (all
+// partial sums are integers below 2^24), so results are bit-exact.
 //
 // Selection keeps the K smallest keys (distance, row-major offset) in a
 // per-thread max-heap in shared memory; the output is sorted ascending.
@@ -151,7 +152,10 @@ __device__ void stage_tile(const DirectParams& P, float* tile, int Yl, int Xl, i
 }
 
 // Register-blocked kernel for a compile-time patch P, channels C, window NX.
-template <int PP, int CC, int NX, bool kU8>
+// kG: read the image from global memory (through L1) instead of a staged
+// tile -- for unions too large to stage; the shared memory then holds only
+// the selection state, so more warps fit on an SM.
+template <int PP, int CC, int NX, bool kU8, bool kG>
 __global__ void __launch_bounds__(128)
 direct_tpl_kernel(DirectParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -162,10 +166,10 @@ direct_tpl_kernel(DirectParams P) {
     const int TY = (TRy - 1) * P.s + NX + PP - 1;
     const int TX = 31 * P.s + NX + PP - 1;
     float* tile = reinterpret_cast<float*>(smem);
-    size_t tile_bytes = ((size_t)TY * TX * CC * 4 + 15) & ~size_t(15);
+    size_t tile_bytes = kG ? 0 : ((size_t)TY * TX * CC * 4 + 15) & ~size_t(15);
     unsigned long long* heaps = reinterpret_cast<unsigned long long*>(smem + tile_bytes);
     unsigned long long* bufs = heaps + (size_t)blockDim.x * P.K;
-    stage_tile<kU8>(P, tile, Yl, Xl, TY, TX);
+    if (!kG) stage_tile<kU8>(P, tile, Yl, Xl, TY, TX);
     BufferedTopK top;
     top.init(heaps, bufs, threadIdx.x, blockDim.x, P.K);
     __syncthreads();
@@ -173,9 +177,16 @@ direct_tpl_kernel(DirectParams P) {
     const int ry = ry0 + threadIdx.x / 32, rx = rx0 + threadIdx.x % 32;
     if (ry >= P.n_ry) return;  // whole warp (one reference row per warp)
     const bool lane_ok = rx < P.n_rx;
-    const int yr = ry * P.s, xr = rx * P.s;
+    const int yr = ry * P.s, xr = min(rx, P.n_rx - 1) * P.s;
     const int Hc = P.H - PP + 1, Wc = P.W - PP + 1;
     const int rowf = TX * CC;
+    // image element (y, x, c) as float, zero outside the image (global source)
+    auto px = [&](int y, int x, int c) -> float {
+        if (x < 0 || x >= P.W) return 0.f;
+        const size_t i = ((size_t)y * P.W + x) * CC + c;
+        return kU8 ? (float)__ldg(static_cast<const uint8_t*>(P.img) + i)
+                   : __ldg(static_cast<const float*>(P.img) + i);
+    };
     const int ylo = max(0, yr - h), yhi = min(Hc - 1, yr + h);  // warp-uniform
     for (int y = ylo; y <= yhi; ++y) {
         float acc[NX];
@@ -185,14 +196,18 @@ direct_tpl_kernel(DirectParams P) {
         for (int u = 0; u < PP; ++u) {
             const float* trow = tile + (size_t)(y - Yl + u) * rowf + (xr - h - Xl) * CC;
             const float* rrow = tile + (size_t)(yr - Yl + u) * rowf + (xr - Xl) * CC;
-#pragma unroll
+            // channels unrolled up to window 39; wider windows take them one at
+            // a time (one candidate row of registers, no spills)
+            constexpr int kCU = NX <= 39 ? CC : 1;
+#pragma unroll kCU
             for (int c = 0; c < CC; ++c) {
                 float t[NX + PP - 1];
 #pragma unroll
-                for (int i = 0; i < NX + PP - 1; ++i) t[i] = trow[i * CC + c];
+                for (int i = 0; i < NX + PP - 1; ++i)
+                    t[i] = kG ? px(y + u, xr - h + i, c) : trow[i * CC + c];
 #pragma unroll
                 for (int v = 0; v < PP; ++v) {
-                    const float r = rrow[v * CC + c];
+                    const float r = kG ? px(yr + u, xr + v, c) : rrow[v * CC + c];
 #pragma unroll
                     for (int i = 0; i < NX; ++i) {
                         float d = r - t[i + v];
@@ -289,18 +304,41 @@ size_t direct_smem(const Geom& g, int TRy, bool tile) {
     return tb + (size_t)TRy * 32 * (g.K + kBufD) * 8;
 }
 
-template <int PP, int CC, int NX>
+template <int PP, int CC, int NX, bool kG>
 cudaError_t launch_tpl(const DirectParams& P, dim3 grid, size_t sm, bool u8, cudaStream_t st) {
     if (u8) {
-        auto k = direct_tpl_kernel<PP, CC, NX, true>;
+        auto k = direct_tpl_kernel<PP, CC, NX, true, kG>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k<<<grid, P.TRy * 32, sm, st>>>(P);
     } else {
-        auto k = direct_tpl_kernel<PP, CC, NX, false>;
+        auto k = direct_tpl_kernel<PP, CC, NX, false, kG>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k<<<grid, P.TRy * 32, sm, st>>>(P);
     }
     return cudaGetLastError();
+}
+
+// Register-blocked instance for (p, C, window), if one exists.
+template <bool kG>
+bool launch_tpl_any(const Geom& g, const DirectParams& P, dim3 grid, size_t sm, bool u8,
+                    cudaStream_t st, cudaError_t* e) {
+    const int NX = 2 * g.h + 1;
+#define BM_DIRECT_CASE(PP, CC, WW)                                          \
+    if (g.p == PP && g.C == CC && NX == WW) {                                \
+        *e = launch_tpl<PP, CC, WW, kG>(P, grid, sm, u8, st);                \
+        return true;                                                         \
+    }
+    BM_DIRECT_CASE(8, 1, 21)
+    BM_DIRECT_CASE(8, 1, 39)
+    BM_DIRECT_CASE(8, 1, 61)
+    BM_DIRECT_CASE(7, 1, 39)
+    BM_DIRECT_CASE(7, 1, 61)
+    BM_DIRECT_CASE(8, 4, 39)
+    BM_DIRECT_CASE(8, 4, 61)
+    BM_DIRECT_CASE(7, 4, 39)
+    BM_DIRECT_CASE(7, 4, 61)
+#undef BM_DIRECT_CASE
+    return false;
 }
 
 }  // namespace
@@ -314,6 +352,22 @@ cudaError_t launch_direct(const Geom& g, const void* img, int32_t* out_idx, void
     P.out_idx = out_idx;
     P.out_dist = out_dist;
     const size_t kSmemCap = 200 * 1024;
+    const bool u8 = g.dtype == kU8;
+    {
+        // register-blocked: a staged union tile when two or more warps of
+        // references fit, else the image through L1 with four warps
+        int TRy = 4;
+        while (TRy > 2 && direct_smem(g, TRy, true) > kSmemCap) TRy /= 2;
+        const bool staged = direct_smem(g, TRy, true) <= kSmemCap;
+        if (!staged) TRy = 4;
+        P.TRy = TRy;
+        const size_t sm = direct_smem(g, TRy, staged);
+        dim3 grid((g.n_rx + 31) / 32, (g.n_ry + TRy - 1) / TRy);
+        cudaError_t e = cudaSuccess;
+        if (staged ? launch_tpl_any<false>(g, P, grid, sm, u8, st, &e)
+                   : launch_tpl_any<true>(g, P, grid, sm, u8, st, &e))
+            return e;
+    }
     int TRy = 4;
     bool tile = true;
     while (TRy > 1 && direct_smem(g, TRy, true) > kSmemCap) TRy /= 2;
@@ -325,14 +379,6 @@ cudaError_t launch_direct(const Geom& g, const void* img, int32_t* out_idx, void
     P.TRy = TRy;
     size_t sm = direct_smem(g, TRy, tile);
     dim3 grid((g.n_rx + 31) / 32, (g.n_ry + TRy - 1) / TRy);
-    const bool u8 = g.dtype == kU8;
-    const int NX = 2 * g.h + 1;
-    if (tile) {
-        if (g.p == 8 && g.C == 1 && NX == 39) return launch_tpl<8, 1, 39>(P, grid, sm, u8, st);
-        if (g.p == 8 && g.C == 1 && NX == 21) return launch_tpl<8, 1, 21>(P, grid, sm, u8, st);
-        if (g.p == 7 && g.C == 1 && NX == 61) return launch_tpl<7, 1, 61>(P, grid, sm, u8, st);
-        if (g.p == 8 && g.C == 4 && NX == 39) return launch_tpl<8, 4, 39>(P, grid, sm, u8, st);
-    }
     if (u8) {
         auto k = tile ? direct_generic_kernel<true, true> : direct_generic_kernel<true, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -164,6 +164,27 @@ def test_uneven_batch_of_32_in_one_call(ctx):
         compare(a, p, win, s, K, idx.cpu().numpy(), dist.cpu().numpy(), refs=refs, threads=0)
 
 
+DIRECT_SHAPES = [
+    # the direct kernel's register-blocked shapes (staged union tile, or the
+    # image through L1 for the 4-channel window-61 unions), ragged edges
+    ("d_p7_c1_w39_f32", 130, 121, 1, "f32", 7, 39, 4, 32),
+    ("d_p8_c1_w61_u8", 140, 133, 1, "u8", 8, 61, 3, 16),
+    ("d_p7_c4_w39_u8", 120, 117, 4, "u8", 7, 39, 4, 70),
+    ("d_p7_c4_w61_f32", 131, 125, 4, "f32", 7, 61, 4, 16),
+    ("d_p8_c4_w61_u8", 129, 140, 4, "u8", 8, 61, 3, 70),
+    ("d_p8_c4_w61_f32", 110, 97, 4, "f32", 8, 61, 3, 32),
+]
+
+
+@pytest.mark.parametrize("case", DIRECT_SHAPES, ids=[c[0] for c in DIRECT_SHAPES])
+def test_direct_kernel_shapes(ctx, case):
+    name, H, W, C, dt, p, win, s, K = case
+    img = make_image(H, W, C, dt, seed=zlib.crc32(name.encode()) % 10007,
+                     sigma=20.0 if C == 4 else 25.0)
+    gidx, gdist = run(ctx, img, p, win, s, K, "direct")
+    compare(img, p, win, s, K, gidx, gdist, threads=0)
+
+
 def test_selfconv_equals_direct_bitwise_on_u8(ctx):
     img = make_image(200, 180, 1, "u8", seed=5)
     a = run(ctx, img, 8, 39, 3, 16, "selfconv")
