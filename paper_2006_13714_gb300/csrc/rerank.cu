@@ -114,7 +114,8 @@ __device__ __forceinline__ float direct_f32(const PairSrc& X, int p_rt, int C_rt
                                             int yc, int xc) {
     const int p = FP ? FP : p_rt, C = FC ? FC : C_rt;
     const int pc = p * C, np = pc >> 1;
-    unsigned long long acc = 0ull;
+    // two packed running sums (even and odd patch rows) halve the dependent chain
+    unsigned long long acc[2] = {0ull, 0ull};
     float tail = 0.f;
     const float2* cbase = X.at(yc, xc);
 #pragma unroll
@@ -125,14 +126,15 @@ __device__ __forceinline__ float direct_f32(const PairSrc& X, int p_rt, int C_rt
         for (int t = 0; t < np; ++t) {
             unsigned long long d;
             asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(rrow[2 * t])), "l"(f2_bits(crow[2 * t])));
-            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc) : "l"(d));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[u & 1]) : "l"(d));
         }
         if (pc & 1) {
             const float d = rrow[pc - 1].x - crow[pc - 1].x;
             tail = fmaf(d, d, tail);
         }
     }
-    return (__uint_as_float((unsigned)acc) + __uint_as_float((unsigned)(acc >> 32))) + tail;
+    return ((__uint_as_float((unsigned)acc[0]) + __uint_as_float((unsigned)(acc[0] >> 32))) +
+            (__uint_as_float((unsigned)acc[1]) + __uint_as_float((unsigned)(acc[1] >> 32)))) + tail;
 }
 
 // The same sum elementwise in order (global-memory source).
@@ -185,15 +187,43 @@ __device__ __forceinline__ void warp_rank(const unsigned long long (&key)[S], in
     }
 }
 
+// One key per lane: odd-even transposition steps (lane pairs exchange
+// out-of-order keys) until the keys ascend with the lane index, at most
+// `steps` of them.  True when sorted (then rank = lane).  The band arrives
+// close to sorted -- the pool is ordered by its estimate -- so a few steps
+// usually suffice.
+__device__ __forceinline__ bool sort_lanes(unsigned long long& k, int lane, int steps) {
+    for (int st = 0; st <= steps; ++st) {
+        const unsigned long long prev = __shfl_up_sync(0xffffffffu, k, 1);
+        if (__all_sync(0xffffffffu, lane == 0 || prev <= k)) return true;
+        if (st == steps) break;
+        const int par = st & 1;
+        const bool lower = ((lane - par) & 1) == 0;
+        const int partner = lower ? lane + 1 : lane - 1;
+        const bool valid = partner >= 0 && partner < 32;
+        const unsigned long long o = __shfl_sync(0xffffffffu, k, valid ? partner : lane);
+        if (valid) k = lower ? (o < k ? o : k) : (o > k ? o : k);
+    }
+    return false;
+}
+
 // Final selection: members carry key (float(d32) bits << 32 | offset);
 // non-members carry kNone.  FP64 refinement at the K-th boundary, then write
 // ranks < K (and the padding).
 template <int S, class Src, class T>
 __device__ void select_and_write(const RerankParams& P, const RerankJob& J, const Src& X,
-                                 const T* ref, const unsigned long long (&key)[S], int nb,
+                                 const T* ref, const unsigned long long (&key_in)[S], int nb,
                                  int lane, size_t r) {
+    unsigned long long key[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) key[i] = key_in[i];
     int rank[S];
-    warp_rank(key, rank);
+    bool ranked = false;
+    if constexpr (S == 1) {
+        ranked = sort_lanes(key[0], lane, 6);
+        rank[0] = lane;
+    }
+    if (!ranked) warp_rank(key, rank);
     double d64[S];
     bool refined[S];
 #pragma unroll
