@@ -383,6 +383,39 @@ def serve_stream(ctx, pkg, synth, dev, n=2000, seed=SEED_BASE + 55, side=2048):
     return out
 
 
+def tiny_row(ctx, pkg, synth, dev, stream):
+    """The tiny plain-method configuration: one 64x64 uint8 image, patch 8,
+    stride 1 (all 57 x 57 references), window 21, K 16, matched alone
+    through bm_match (its windows split across CTAs: window_split parts per
+    tile) -- latency from CUDA events, median of 50 calls after warm-up."""
+    import torch
+    img = torch.from_numpy(synth.gray(64, 64, 25.0, SEED_BASE + 1, np.uint8)).to(dev)
+    idx, dist_t = ctx.outputs(img, 8, 1, 16)
+    for _ in range(5):
+        ctx.match(img, 8, 21, 1, 16, out=(idx, dist_t), stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    for _ in range(50):
+        e0.record(stream)
+        ctx.match(img, 8, 21, 1, 16, out=(idx, dist_t), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        lat.append(e0.elapsed_time(e1))
+    med = statistics.median(lat)
+    e0.record(stream)
+    for _ in range(20):
+        ctx.match_direct(img, 8, 21, 1, 16, out=(idx, dist_t), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    d_ms = e0.elapsed_time(e1) / 20
+    return {"workload": "64x64 uint8 grey, patch 8, stride 1, window 21, K 16, alone (bm_match)",
+            "latency_ms": {"median": med, "min": min(lat)},
+            "ref_patches_per_s": 57 * 57 / (med / 1e3),
+            "window_split": pkg.bm_window_split(64, 64, 1, pkg.BM_U8, 8, 21, 1, 16),
+            "direct_fp32_gpu_ms": d_ms}
+
+
 def batch_row(ctx, pkg, dev, nps, p, win, s, K, label, peaks, steps=5, n_direct=None):
     """Throughput of one batch workload through bm_match_batch (the graph-
     captured persistent launches): ref-patches/s, useful cross-term TMAC/s
@@ -797,6 +830,7 @@ def run_ours(args, world, rank, local, dist):
     cfg4 = batch_row(ctx, pkg, dev, rgbnir16,
                      8, 39, 3, 32, "16 uint8 RGB-NIR 1024x1024x4 images, patch 8, stride 3, window 39, K 32",
                      peaks, n_direct=4)
+    tiny = tiny_row(ctx, pkg, synth, dev, stream)
     serve = serve_stream(ctx, pkg, synth, dev, n=args.serve_requests) if not args.no_serve else None
     groups = groups_throughput(ctx, imgs, outs, peaks, stream, dev)
     nlm = nlm_throughput(ctx, imgs, stream, dev, pairs)
@@ -839,6 +873,7 @@ def run_ours(args, world, rank, local, dist):
         "clocks": clk,
         "stage_ms_share": stage_share,
         "kernel_ms_per_step_with_stage_events": staged_ms,
+        "config1_tiny": tiny,
         "config3_batch": cfg3,
         "config4_rgbnir": cfg4,
         "serve": serve,
@@ -848,7 +883,8 @@ def run_ours(args, world, rank, local, dist):
         "match_3d": m3d,
         "direct_fp32_gpu": {"ms_per_image": direct_ms_img, "ms_per_image_selfconv": tc_ms_img,
                             "speedup": direct_ms_img / tc_ms_img},
-        "single_image_latency_ms": {"min": min(lat), "median": statistics.median(lat)},
+        "single_image_latency_ms": {"min": min(lat), "median": statistics.median(lat),
+                                    "window_split": pkg.bm_window_split(H, W, 1, pkg.BM_F32, p, win, s, K)},
         "stats": {k: st1[k] - st0[k] for k in ("rerank_overflow", "fp64_rechecks",
                                                "bound_violations", "tc_jobs")},
     }

@@ -401,6 +401,30 @@ int bm_static_check(bm_stream stream);
  * 0 cancels.  BM_ERR_INVALID for any other mode. */
 int bm_static_set_fault_injection(int mode);
 
+/*
+ * Device workspace (bytes) a context allocates for this job with the
+ * default algorithm: operand planes, norms, float32 candidate pool, window-
+ * split part lists, status words.  0 when the job runs on the direct kernel
+ * (no workspace) or the arguments are invalid.  Admission under a context's
+ * memory budget (bm_create, bm_submit) counts these bytes.  Host only.
+ */
+size_t bm_workspace_bytes(int H, int W, int C, bm_dtype dtype, int patch, int window, int stride,
+                          int K);
+
+/*
+ * Window split (host only, no device work): the number of parts each tile's
+ * search window is split into when this job runs alone through bm_match,
+ * bm_match_batch or bm_submit on the tensor-core path.  A launch whose
+ * tiles (128 references each) are too few to occupy every SM of the GPU
+ * splits each tile's union of windows into 2 or 4 column ranges that
+ * separate CTAs run; each part keeps its own top-K list (float32: pool),
+ * and a merge kernel combines them, so results are identical to an unsplit
+ * run.  A launch with enough tiles (a batch of many images) does not split.
+ * Returns 1 (no split), 2 or 4; 0 for invalid arguments.  bm_match_static
+ * never splits.
+ */
+int bm_window_split(int H, int W, int C, bm_dtype dtype, int patch, int window, int stride, int K);
+
 /* Scratch bytes bm_match_static needs for this job (0 if the arguments are
  * invalid or unsupported).  Host only. */
 size_t bm_static_scratch_bytes(int H, int W, int C, bm_dtype dtype,

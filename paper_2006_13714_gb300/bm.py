@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
             "bm_set_timing": ([vp, ci], ci),
             "bm_get_timing": ([vp, ctypes.POINTER(bm_timing), ci], ci),
             "bm_static_scratch_bytes": ([ci, ci, ci, ci, ci, ci, ci, ci], sz),
+            "bm_window_split": ([ci, ci, ci, ci, ci, ci, ci, ci], ci),
+            "bm_workspace_bytes": ([ci, ci, ci, ci, ci, ci, ci, ci], sz),
             "bm_match_static": ([vp, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp], ci),
             "bm_static_init": ([], ci),
             "bm_static_check": ([vp], ci),
@@ -145,6 +147,14 @@ def bm_match_direct(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx,
                     stream) -> int:
     return load().bm_match_direct(ctx, img, H, W, C, dtype, patch, window, stride, K, out_idx,
                                   out_dist, stream)
+
+
+def bm_workspace_bytes(H, W, C, dtype, patch, window, stride, K) -> int:
+    return load().bm_workspace_bytes(H, W, C, dtype, patch, window, stride, K)
+
+
+def bm_window_split(H, W, C, dtype, patch, window, stride, K) -> int:
+    return load().bm_window_split(H, W, C, dtype, patch, window, stride, K)
 
 
 def bm_static_scratch_bytes(H, W, C, dtype, patch, window, stride, K) -> int:

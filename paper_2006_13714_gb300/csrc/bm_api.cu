@@ -133,7 +133,8 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Byte layout of one tensor-core job's workspace.
 struct WsLayout {
-    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, status, total;
+    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, status, split, total;
+    int wsplit;
 };
 
 WsLayout ws_layout(const Geom& g) {
@@ -146,6 +147,10 @@ WsLayout ws_layout(const Geom& g) {
     l.pool_idx = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
     l.pool_score = off; off += g.dtype == kF32 ? align256((size_t)g.nR * g.L * 4) : 0;
     l.status = off; off += 256;
+    // window split: the parts' lists (offsets, then distances / score bits)
+    l.wsplit = tc_window_split(g);
+    const size_t nlist = (size_t)g.nR * (g.dtype == kF32 ? g.L : g.K);
+    l.split = off; off += l.wsplit > 1 ? 2 * align256((size_t)l.wsplit * nlist * 4) : 0;
     l.total = off;
     return l;
 }
@@ -390,6 +395,12 @@ void job_views(const Geom& g, const bm_request& r, void* ws, PrepJob& pj, TcArgs
     } else {
         a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
         a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
+    }
+    if (l.wsplit > 1) {
+        const size_t nlist = (size_t)g.nR * (g.dtype == kF32 ? g.L : g.K);
+        a.wsplit = l.wsplit;
+        a.split_idx = reinterpret_cast<int32_t*>(b + l.split);
+        a.split_val = reinterpret_cast<int32_t*>(b + l.split + align256((size_t)l.wsplit * nlist * 4));
     }
 }
 
@@ -735,6 +746,19 @@ void worker_loop(bm_ctx* ctx) {
 }  // namespace
 
 extern "C" {
+
+size_t bm_workspace_bytes(int H, int W, int C, bm_dtype dtype, int patch, int window, int stride,
+                          int K) {
+    Geom g;
+    if (make_geom(g, H, W, C, (int)dtype, patch, window, stride, K) != 0) return 0;
+    return tc_supported(g) ? ws_layout(g).total : 0;
+}
+
+int bm_window_split(int H, int W, int C, bm_dtype dtype, int patch, int window, int stride, int K) {
+    Geom g;
+    if (make_geom(g, H, W, C, (int)dtype, patch, window, stride, K) != 0) return 0;
+    return tc_supported(g) ? tc_window_split(g) : 1;
+}
 
 int bm_num_refs(int H, int W, int patch, int stride, int* n_ry, int* n_rx) {
     if (H < 1 || W < 1 || patch < 1 || stride < 1 || patch > H || patch > W)

@@ -152,6 +152,14 @@ struct TcArgs {
     int* status;              // device error word (0 = ok)
     int* fault = nullptr;     // nullable: context-wide sticky word, first timeout code kept
     int inject = 0;           // test hook: 1 = the producer skips publishing its first stage
+    // window split (nullable): room for up to `wsplit` part lists of the job
+    // ([wsplit][nR][N] offsets and distances / score bits, N = K for uint8,
+    // L for float32).  A launch that leaves SMs idle splits each tile's
+    // window into parts that separate CTAs run, then merges the parts' lists
+    // into the outputs (uint8) or the pool (float32).
+    int wsplit = 1;
+    int32_t* split_idx = nullptr;
+    int32_t* split_val = nullptr;
 };
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st);
 // Several jobs in persistent launches (consecutive jobs of one class share a
@@ -166,6 +174,9 @@ bool tc_supported(const Geom& g);
 // 2^bits ulp (0: exact float32 scores).
 int tc_score_bits(const Geom& g);
 bool tc_same_class(const Geom& a, const Geom& b);
+// Parts per tile the window split may use for a job (1: never split);
+// TcArgs.wsplit and the part-list room follow it.
+int tc_window_split(const Geom& g);
 
 // (a6) float32 boundary re-rank: direct recomputation of the pool's band,
 // FP64 only for ties at the K-th boundary; writes the final outputs.

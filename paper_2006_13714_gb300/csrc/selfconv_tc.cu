@@ -53,6 +53,7 @@
 #include "bm_internal.h"
 
 #include <cuda.h>
+#include <algorithm>
 #include <cuda_bf16.h>
 
 namespace bm {
@@ -99,10 +100,17 @@ struct TcJob {
     float* pool_score;
     int* status;              // nullable: the job's error word (timeout code on abort)
     int H, W, n_ry, n_rx, Hc, Wc;
-    int tiles_x, tile_begin;  // tiles along x; index of the job's first tile
+    int tiles_x, tile_begin;  // tiles along x; index of the job's first tile (part)
+    int wsplit;               // window split: parts per tile (1: none); part q's lists
+                              // are references q * nR .. of the output arrays
 };
 
 constexpr int kMaxJobs = 64;  // jobs per launch (kept inline in the kernel parameters)
+// Window split: a launch whose tiles number fewer than kSplitTarget per
+// tile slot splits each job's windows into up to kMaxSplit parts (work
+// items), so that small jobs still occupy every SM of a GB300.
+constexpr int kSplitTarget = 152;
+constexpr int kMaxSplit = 4;
 
 struct TcParams {
     TcGeom g;
@@ -595,10 +603,14 @@ struct TileInfo {
     const TcJob* job;
     int ry0, rx0, ry_last, rx_last;
     int Y0, X0, NR, NX, nchunks, center_chunk;
+    int part, c0, c1;  // window split: this part's chunks [c0, c1) of the visiting order
 };
 
-// Tile t of the launch: its job (binary search over the jobs' first tiles)
-// and the union of its references' clipped windows.
+// Work item t of the launch: its job (binary search over the jobs' first
+// items), its tile, the union of the tile's references' clipped windows,
+// and -- when the job's windows are split -- the part of that union's
+// candidate columns this item covers (chunks [c0, c1) of the visiting order;
+// the parts of a tile are consecutive items, so they land on different CTAs).
 __device__ __forceinline__ TileInfo tile_info(const TcParams& P, int t) {
     const TcGeom& G = P.g;
     int lo = 0, hi = P.njobs - 1;
@@ -610,7 +622,9 @@ __device__ __forceinline__ TileInfo tile_info(const TcParams& P, int t) {
     TileInfo T;
     T.job = &P.jobs[lo];
     const TcJob& J = *T.job;
-    const int lt = t - J.tile_begin;
+    const int li = t - J.tile_begin;
+    const int lt = li / J.wsplit;
+    T.part = li - lt * J.wsplit;
     T.ry0 = (lt / J.tiles_x) * G.ty;
     T.rx0 = (lt % J.tiles_x) * G.tx;
     T.ry_last = min(T.ry0 + G.ty - 1, J.n_ry - 1);
@@ -623,6 +637,8 @@ __device__ __forceinline__ TileInfo tile_info(const TcParams& P, int t) {
     T.NX = X1 - T.X0 + 1;
     T.nchunks = (T.NX + G.kcols - 1) / G.kcols;
     T.center_chunk = min(T.nchunks - 1, ((T.rx0 + T.rx_last) * G.s / 2 - T.X0) / G.kcols);
+    T.c0 = T.part * T.nchunks / J.wsplit;
+    T.c1 = (T.part + 1) * T.nchunks / J.wsplit;
     return T;
 }
 
@@ -804,7 +820,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             // (4) chunks: stage free -> split norms by bulk copy -> strips
             // formed in place -> arrival on the stage's barrier
             const int rows = min(G.Rb, J.Hc - T.Y0);
-            for (int c = 0; c < T.nchunks; ++c, ++cs) {
+            for (int c = T.c0; c < T.c1; ++c, ++cs) {
                 const int stage = cs % G.nst, use = cs / G.nst;
                 if (use > 0 && !__all_sync(0xffffffffu, mbar_wait(BAR(k, kBarSEmpty + stage), (use - 1) & 1, abort_flag, 1))) {
                     ok = false;
@@ -834,7 +850,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 __syncwarp();
                 // (the test hook withholds this arrival once: the MMA warp's bounded
                 // wait on the stage then runs out and the CTA takes its abort path)
-                const bool withhold = P.inject && cta == 0 && k == 0 && turn == 0 && c == 0;
+                const bool withhold = P.inject && cta == 0 && k == 0 && turn == 0 && c == T.c0;
                 if (lane == 0 && !withhold) mbar_arrive(BAR(k, kBarFull + stage));
             }
         }
@@ -869,7 +885,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 if (tile >= P.total_tiles) break;
                 const TileInfo T = tile_info(P, tile);
                 if (!mbar_wait(BAR(k, kBarAFull), turn & 1, abort_flag, 7)) break;
-                for (int c = 0; c < T.nchunks; ++c, ++cs) {
+                for (int c = T.c0; c < T.c1; ++c, ++cs) {
                     const int stage = cs % G.nst, use = cs / G.nst;
                     const int buf = cs & 1, ub = cs >> 1;
                     if (ub > 0 && !mbar_wait(BAR(k, kBarTEmpty + buf), (ub - 1) & 1, abort_flag, 2)) {
@@ -906,7 +922,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
                     mma_commit(BAR(k, kBarSEmpty + stage));
                     mma_commit(BAR(k, kBarTFull + buf));
-                    if (c + 1 == T.nchunks) mma_commit(BAR(k, kBarAEmpty));  // A free once these finish
+                    if (c + 1 == T.c1) mma_commit(BAR(k, kBarAEmpty));  // A free once these finish
                 }
             }
             // drain: every MMA issued by this thread finishes before TMEM is freed
@@ -968,7 +984,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             float thr = -__int_as_float(0x7f800000);  // -inf while the list has empty slots
             int cnt = 0;
             const int merge_at = min(kMergeAt, G.kbuf - 15);  // room for one more block
-            for (int c = 0; c < T.nchunks; ++c, ++qc) {
+            for (int c = T.c0; c < T.c1; ++c, ++qc) {
                 const int buf = qc & 1, ub = qc >> 1;
                 if (!mbar_wait(BAR(k, kBarTFull + buf), ub & 1, abort_flag, 4)) break;
                 tc_fence_after();
@@ -1058,7 +1074,8 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             }
             // ---- write results
             if (lane_ok && !*abort_flag) {
-                const size_t ref = (size_t)ry * J.n_rx + rx;
+                // a window part writes its own list (merged by split_merge_kernel)
+                const size_t ref = (size_t)ry * J.n_rx + rx + (size_t)T.part * J.n_ry * J.n_rx;
                 if constexpr (LC == 0) heap.sort();  // outputs and pools best first
                 const int nout = kF32 ? G.HL : G.K;
                 auto emit = [&](int i, unsigned long long key) {
@@ -1259,6 +1276,23 @@ bool encode_plane(CUtensorMap* m, const uint16_t* plane, const Geom& g, const Tc
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Parts per tile for job g under class geometry t: a power of two up to
+// cap, no larger than the fewest chunks of any of its tiles (the union of
+// windows narrows at the left and right image edges), so that every part
+// has at least one chunk of candidate columns.
+int split_cap(const Geom& g, const TcGeom& t, int cap) {
+    const int tiles_x = (g.n_rx + t.tx - 1) / t.tx;
+    int min_chunks = 1 << 30;
+    for (int bx = 0; bx < tiles_x; ++bx) {
+        const int rx0 = bx * t.tx, rx_last = std::min(rx0 + t.tx - 1, g.n_rx - 1);
+        const int X0 = std::max(0, rx0 * g.s - g.h), X1 = std::min(g.Wc - 1, rx_last * g.s + g.h);
+        min_chunks = std::min(min_chunks, (X1 - X0 + 1 + t.kcols - 1) / t.kcols);
+    }
+    int w = 1;
+    while (w * 2 <= cap && w * 2 <= min_chunks) w *= 2;
+    return w;
+}
+
 bool make_job(TcJob& j, const Geom& g, const TcGeom& t, const TcArgs& a, int tile_begin) {
     j = TcJob{};
     if (!encode_plane(&j.map[0], a.plane0, g, t)) return false;
@@ -1273,7 +1307,67 @@ bool make_job(TcJob& j, const Geom& g, const TcGeom& t, const TcArgs& a, int til
     j.tiles_x = (g.n_rx + t.tx - 1) / t.tx;
     j.tile_begin = tile_begin;
     j.status = a.status;
+    j.wsplit = 1;
     return true;
+}
+
+// Window-split merge: the parts' sorted lists of one reference merged into
+// the first N entries by the lists' own order -- uint8: (distance, offset)
+// ascending; float32 pool: (score descending, offset ascending) -- with
+// empty entries (offset -1) last.  Every candidate is in exactly one part,
+// so the result equals the list one pass over the whole window keeps.
+struct MergeJob {
+    const int32_t* idx;  // [wsplit][nR][N]
+    const int32_t* val;  // distances (uint8) or score bits (float32), same layout
+    int32_t* out_idx;    // [nR][N]
+    int32_t* out_val;
+    int nR, wsplit, ref_begin;
+};
+struct MergeParams {
+    int N, f32, njobs, total;
+    MergeJob jobs[kMaxJobs];
+};
+
+__global__ void __launch_bounds__(256) split_merge_kernel(const __grid_constant__ MergeParams P) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.total) return;
+    int lo = 0, hi = P.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].ref_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const MergeJob& J = P.jobs[lo];
+    const int r = t - J.ref_begin;
+    int pos[4] = {0, 0, 0, 0};
+    for (int i = 0; i < P.N; ++i) {
+        int bq = 0;
+        int32_t bid = 0, bv = 0;
+        for (int q = 0; q < J.wsplit; ++q) {
+            const int ps = pos[q] < P.N ? pos[q] : P.N - 1;
+            const size_t e = ((size_t)q * J.nR + r) * P.N + ps;
+            const int32_t id = pos[q] < P.N ? J.idx[e] : -1;
+            const int32_t v = J.val[e];
+            bool better;
+            if (q == 0) better = true;
+            else if (id < 0) better = false;
+            else if (bid < 0) better = true;
+            else if (P.f32) {
+                const float a = __int_as_float(v), b = __int_as_float(bv);
+                better = a > b || (a == b && id < bid);
+            } else {
+                better = v < bv || (v == bv && id < bid);
+            }
+            if (better) {
+                bq = q;
+                bid = id;
+                bv = v;
+            }
+        }
+        J.out_idx[(size_t)r * P.N + i] = bid;
+        J.out_val[(size_t)r * P.N + i] = bv;
+        ++pos[bq];
+    }
 }
 
 cudaError_t launch_params(TcParams& P, cudaStream_t st) {
@@ -1344,6 +1438,7 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         P.fault = as[i].fault;
         P.inject = as[i].inject;
         int tiles = 0, nj = 0;
+        const int first = i;
         while (i < n && nj < kMaxJobs && tc_same_class(gs[i], gs[i - nj]) &&
                (choices ? choices[i] : -1) == choice) {
             if (!make_job(P.jobs[nj], gs[i], P.g, as[i], tiles)) return cudaErrorInvalidValue;
@@ -1351,13 +1446,64 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
             ++nj;
             ++i;
         }
+        // window split: only when the launch's tiles alone leave SMs idle, and
+        // then for every job that has part lists (wsplit of its arguments)
+        const bool split = (long long)tiles < (long long)kSplitTarget * P.g.nslots;
+        MergeParams M{};
+        M.N = P.g.f32 ? P.g.HL : P.g.K;
+        M.f32 = P.g.f32;
+        tiles = 0;
+        for (int j = 0; j < nj; ++j) {
+            const TcArgs& a = as[first + j];
+            TcJob& J = P.jobs[j];
+            J.tile_begin = tiles;
+            const int jt = J.tiles_x * ((J.n_ry + P.g.ty - 1) / P.g.ty);
+            const int w = (split && a.split_idx && a.split_val) ? split_cap(gs[first + j], P.g, a.wsplit) : 1;
+            if (w > 1) {
+                J.wsplit = w;
+                MergeJob& m = M.jobs[M.njobs++];
+                m.nR = J.n_ry * J.n_rx;
+                m.wsplit = w;
+                m.ref_begin = M.total;
+                m.idx = a.split_idx;
+                m.val = a.split_val;
+                M.total += m.nR;
+                if (P.g.f32) {
+                    m.out_idx = J.pool_idx;
+                    m.out_val = reinterpret_cast<int32_t*>(J.pool_score);
+                    J.pool_idx = a.split_idx;
+                    J.pool_score = reinterpret_cast<float*>(a.split_val);
+                } else {
+                    m.out_idx = J.out_idx;
+                    m.out_val = J.out_dist;
+                    J.out_idx = a.split_idx;
+                    J.out_dist = a.split_val;
+                }
+            }
+            tiles += jt * J.wsplit;
+        }
         P.njobs = nj;
         P.total_tiles = tiles;
         cudaError_t e = launch_params(P, st);
         if (e != cudaSuccess) return e;
         if (nlaunch) ++*nlaunch;
+        if (M.njobs) {
+            split_merge_kernel<<<(M.total + 255) / 256, 256, 0, st>>>(M);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (nlaunch) ++*nlaunch;
+        }
     }
     return cudaSuccess;
+}
+
+int tc_window_split(const Geom& g) {
+    TcGeom t{};
+    if (!make_tc_geom(g, t)) return 1;
+    const long long items = (long long)((g.n_rx + t.tx - 1) / t.tx) * ((g.n_ry + t.ty - 1) / t.ty);
+    const long long want = (long long)kSplitTarget * t.nslots;
+    int cap = 1;
+    while (cap < kMaxSplit && items * cap < want) cap *= 2;
+    return split_cap(g, t, cap);
 }
 
 }  // namespace bm

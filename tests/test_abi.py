@@ -56,3 +56,24 @@ def test_create_fails_loudly_without_gpu():
     with pytest.raises(B.BMError) as e:
         B.bm_create(0)
     assert e.value.code in (B.BM_ERR_CUDA, B.BM_ERR_INVALID)
+
+
+def test_window_split_query():
+    # small jobs split their windows (alone they leave SMs idle), large ones do not
+    assert B.bm_window_split(64, 64, 1, B.BM_U8, 8, 21, 1, 16) == 4
+    assert B.bm_window_split(2048, 2048, 1, B.BM_F32, 8, 39, 3, 16) == 1
+    assert B.bm_window_split(64, 64, 1, B.BM_U8, 8, 22, 1, 16) == 0  # even window: invalid
+    for args in [(96, 88, 1, B.BM_F32, 8, 39, 3, 16), (150, 133, 1, B.BM_F32, 7, 61, 4, 70),
+                 (80, 72, 4, B.BM_U8, 8, 39, 3, 32), (8, 12, 1, B.BM_U8, 8, 7, 1, 5)]:
+        assert B.bm_window_split(*args) in (1, 2, 4)
+
+
+def test_workspace_bytes_query():
+    # the context workspace holds at least the static path's buffers, plus
+    # the window split's part lists when the job splits
+    for args in [(96, 96, 1, B.BM_F32, 8, 39, 3, 16), (512, 512, 1, B.BM_F32, 8, 39, 3, 16),
+                 (64, 64, 1, B.BM_U8, 8, 21, 1, 16)]:
+        ws = B.bm_workspace_bytes(*args)
+        assert ws >= B.bm_static_scratch_bytes(*args) - 256 > 0
+    assert B.bm_workspace_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 0  # direct kernel
+    assert B.bm_workspace_bytes(64, 64, 1, B.BM_U8, 8, 22, 1, 16) == 0      # invalid

@@ -185,6 +185,45 @@ def test_direct_kernel_shapes(ctx, case):
     compare(img, p, win, s, K, gidx, gdist, threads=0)
 
 
+SPLIT_CASES = [
+    # jobs small enough that alone they split their windows (bm_window_split > 1)
+    ("u8_64", 64, 64, 1, "u8", 8, 21, 1, 16),
+    ("f32_96x88", 96, 88, 1, "f32", 8, 39, 3, 16),
+    ("f32_k70", 150, 133, 1, "f32", 7, 61, 4, 70),
+    ("u8_c4", 80, 72, 4, "u8", 8, 39, 3, 32),
+]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_window_split_equals_unsplit(ctx, case):
+    """A job alone splits each tile's window across CTAs and merges the
+    parts' lists; the same job inside a batch large enough to occupy the GPU
+    runs unsplit.  The two must agree bit for bit (uint8 outputs, float32
+    outputs after the re-rank of the merged pool)."""
+    name, H, W, C, dt, p, win, s, K = case
+    code = B.BM_U8 if dt == "u8" else B.BM_F32
+    assert B.bm_window_split(H, W, C, code, p, win, s, K) > 1
+    ny, nx = B.bm_num_refs(H, W, p, s)
+    n = min(64, -(-304 * 128 * 11 // 10 // (ny * nx)) + 1)  # tiles >= 152 x 2 slots
+    imgs, outs, reqs = [], [], []
+    for i in range(n):
+        t = torch.from_numpy(make_image(H, W, C, dt, seed=600 + i)).cuda()
+        idx, dist = ctx.outputs(t, p, s, K)
+        imgs.append(t)
+        outs.append((idx, dist))
+        reqs.append(B.Context.request(t, p, win, s, K, idx, dist))
+    ctx.match_batch(reqs, stream=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    for i in (0, n // 2, n - 1):
+        a_idx, a_dist = ctx.match(imgs[i], p, win, s, K)  # alone: split
+        torch.cuda.synchronize()
+        assert torch.equal(a_idx, outs[i][0]) and torch.equal(a_dist, outs[i][1]), f"image {i}"
+    img0 = make_image(H, W, C, dt, seed=600)
+    a_idx, a_dist = ctx.match(imgs[0], p, win, s, K)
+    torch.cuda.synchronize()
+    compare(img0, p, win, s, K, a_idx.cpu().numpy(), a_dist.cpu().numpy())
+
+
 def test_selfconv_equals_direct_bitwise_on_u8(ctx):
     img = make_image(200, 180, 1, "u8", seed=5)
     a = run(ctx, img, 8, 39, 3, 16, "selfconv")

@@ -87,7 +87,7 @@ def test_budget_admission_and_errors():
     t = torch.from_numpy(img).cuda()
     # a budget that holds about two of these jobs at a time
     probe = B.Context(0)
-    need = B.bm_static_scratch_bytes(96, 96, 1, B.BM_F32, 8, 39, 3, 16)
+    need = B.bm_workspace_bytes(96, 96, 1, B.BM_F32, 8, 39, 3, 16)
     probe.close()
     ctx = B.Context(0, mem_budget_bytes=int(2.5 * need))
     outs = [ctx.outputs(t, 8, 3, 16) for _ in range(6)]
