@@ -415,7 +415,7 @@ size_t bm_workspace_bytes(int H, int W, int C, bm_dtype dtype, int patch, int wi
  * Window split (host only, no device work): the number of parts each tile's
  * search window is split into when this job runs alone through bm_match,
  * bm_match_batch or bm_submit on the tensor-core path.  A launch whose
- * tiles (128 references each) are too few to occupy every SM of the GPU
+ * tiles (128 references each) are fewer than the GPU's 152 SMs
  * splits each tile's union of windows into 2 or 4 column ranges that
  * separate CTAs run; each part keeps its own top-K list (float32: pool),
  * and a merge kernel combines them, so results are identical to an unsplit

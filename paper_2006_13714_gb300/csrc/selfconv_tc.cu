@@ -106,9 +106,13 @@ struct TcJob {
 };
 
 constexpr int kMaxJobs = 64;  // jobs per launch (kept inline in the kernel parameters)
-// Window split: a launch whose tiles number fewer than kSplitTarget per
-// tile slot splits each job's windows into up to kMaxSplit parts (work
-// items), so that small jobs still occupy every SM of a GB300.
+// Window split: a launch whose tiles number fewer than kSplitTarget (the
+// SMs of a GB300) splits each job's windows into up to kMaxSplit parts
+// (work items), so that small jobs still occupy every SM.  Each part keeps
+// its own list, and a part that starts far from the references' centres
+// appends more before its threshold tightens, so the split costs selection
+// work: it pays only where SMs would otherwise idle (a 512 x 512 image
+// alone, 171 tiles, ran 20 % slower split in two).
 constexpr int kSplitTarget = 152;
 constexpr int kMaxSplit = 4;
 
@@ -1446,9 +1450,9 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
             ++nj;
             ++i;
         }
-        // window split: only when the launch's tiles alone leave SMs idle, and
-        // then for every job that has part lists (wsplit of its arguments)
-        const bool split = (long long)tiles < (long long)kSplitTarget * P.g.nslots;
+        // window split: only when the launch's tiles leave SMs idle, and then
+        // for every job that has part lists (wsplit of its arguments)
+        const bool split = tiles < kSplitTarget;
         MergeParams M{};
         M.N = P.g.f32 ? P.g.HL : P.g.K;
         M.f32 = P.g.f32;
@@ -1500,7 +1504,7 @@ int tc_window_split(const Geom& g) {
     TcGeom t{};
     if (!make_tc_geom(g, t)) return 1;
     const long long items = (long long)((g.n_rx + t.tx - 1) / t.tx) * ((g.n_ry + t.ty - 1) / t.ty);
-    const long long want = (long long)kSplitTarget * t.nslots;
+    const long long want = kSplitTarget;
     int cap = 1;
     while (cap < kMaxSplit && items * cap < want) cap *= 2;
     return split_cap(g, t, cap);
