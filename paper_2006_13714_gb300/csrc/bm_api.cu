@@ -200,6 +200,8 @@ struct bm_ctx {
     int* h_ring = nullptr;
     bool ring_busy[kRing] = {};
     cudaStream_t aux_stream = nullptr;  // reads of the fault word and counters
+    std::mutex br_mu;
+    std::unordered_map<cudaStream_t, std::vector<cudaStream_t>> branches;  // class branches per stream
     std::mutex q_mu;
     std::condition_variable q_cv;
     std::deque<uint64_t> pending;
@@ -457,6 +459,22 @@ int enqueue_job(bm_ctx* ctx, const Geom& g, const bm_request& r, void* ws, cudaS
     return finish_job(ctx, g, r, a, st);
 }
 
+// Branch streams of base stream st (created on first use, kept per base
+// stream so that two threads capturing on different streams never share
+// one): out receives n of them.
+int branch_streams(bm_ctx* ctx, cudaStream_t st, int n, std::vector<cudaStream_t>& out) {
+    std::lock_guard<std::mutex> lk(ctx->br_mu);
+    std::vector<cudaStream_t>& v = ctx->branches[st];
+    while ((int)v.size() < n) {
+        cudaStream_t s2 = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "branch stream create");
+        v.push_back(s2);
+    }
+    out.assign(v.begin(), v.begin() + n);
+    return BM_OK;
+}
+
 // Enqueue n validated jobs on st with one workspace (job i at ws + offs[i]):
 // direct jobs, then the preparation kernels of the tensor-core jobs (one
 // launch per stage), their cross term + top-K (persistent launches, one per
@@ -502,30 +520,74 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
         cudaStreamIsCapturing(st, &cap);
         if (cap == cudaStreamCaptureStatusNone) ta[0].inject = ctx->inject.exchange(0);
         const std::vector<int> ch = tc_choices(ctx, tg.data(), ta.data(), (int)tg.size(), st);
-        int nl = 0;
-        cudaError_t e = timed(ctx, BM_STAGE_TC, st, [&] {
-            return launch_tc_batch(tg.data(), ta.data(), (int)tg.size(), st, &nl, ch.data());
-        }, &nl);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
+        // classes: runs of jobs that share one persistent launch (same
+        // tensor-core class and tile choice)
+        std::vector<int> cls_begin;
+        for (int j = 0; j < (int)tg.size(); ++j)
+            if (j == 0 || !tc_same_class(tg[j], tg[j - 1]) || ch[j] != ch[j - 1]) cls_begin.push_back(j);
+        cls_begin.push_back((int)tg.size());
+        const int ncls = (int)cls_begin.size() - 1;
         if (count) ctx->tc_jobs += tc_ids.size();
-        std::vector<Geom> rg;
-        std::vector<RerankArgs> ra;
-        for (int i : tc_ids) {
-            if (gs[i].dtype != kF32) continue;
-            rg.push_back(gs[i]);
-            ra.push_back(RerankArgs{static_cast<const float*>(reqs[i].img),
-                                    static_cast<const float*>(args[i].nrm), args[i].pool_idx,
-                                    args[i].pool_score, reqs[i].out_idx,
-                                    static_cast<float*>(reqs[i].out_dist)});
+        // each class's tensor-core launch and its re-rank; with several
+        // classes (and stage timing off) every class after the first runs on
+        // a branch stream forked from st and joined back, so the classes'
+        // persistent launches overlap: CTAs of one class take the SMs that
+        // another class's CTAs leave.  Under graph capture the branches become
+        // parallel graph branches.
+        const bool fork = ncls > 1 && !ctx->timing.load();
+        std::vector<cudaStream_t> br;
+        if (fork) {
+            int rc = branch_streams(ctx, st, ncls - 1, br);
+            if (rc != BM_OK) return rc;
         }
-        if (!rg.empty()) {
-            int nr = 0;
-            e = timed(ctx, BM_STAGE_RERANK, st, [&] {
-                return launch_rerank_batch(rg.data(), ra.data(), (int)rg.size(), ctx->d_counters,
-                                           st, &nr);
-            }, &nr);
-            if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
+        cudaEvent_t ev_fork = nullptr;
+        std::vector<cudaEvent_t> ev_join;
+        cudaError_t e = cudaSuccess;
+        if (fork) {
+            if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventRecord(ev_fork, st)) != cudaSuccess)
+                return cuda_fail(e, "class fork");
         }
+        for (int c = 0; c < (fork ? ncls : 1); ++c) {
+            const int b = fork ? cls_begin[c] : 0, eidx = fork ? cls_begin[c + 1] : (int)tg.size();
+            cudaStream_t sc = (fork && c > 0) ? br[c - 1] : st;
+            if (sc != st && (e = cudaStreamWaitEvent(sc, ev_fork, 0)) != cudaSuccess)
+                return cuda_fail(e, "class fork");
+            int nl = 0;
+            e = timed(ctx, BM_STAGE_TC, sc, [&] {
+                return launch_tc_batch(tg.data() + b, ta.data() + b, eidx - b, sc, &nl, ch.data() + b);
+            }, &nl);
+            if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel launch");
+            std::vector<Geom> rg;
+            std::vector<RerankArgs> ra;
+            for (int j = b; j < eidx; ++j) {
+                const int i = tc_ids[j];
+                if (gs[i].dtype != kF32) continue;
+                rg.push_back(gs[i]);
+                ra.push_back(RerankArgs{static_cast<const float*>(reqs[i].img),
+                                        static_cast<const float*>(args[i].nrm), args[i].pool_idx,
+                                        args[i].pool_score, reqs[i].out_idx,
+                                        static_cast<float*>(reqs[i].out_dist)});
+            }
+            if (!rg.empty()) {
+                int nr = 0;
+                e = timed(ctx, BM_STAGE_RERANK, sc, [&] {
+                    return launch_rerank_batch(rg.data(), ra.data(), (int)rg.size(), ctx->d_counters,
+                                               sc, &nr);
+                }, &nr);
+                if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel launch");
+            }
+            if (sc != st) {
+                cudaEvent_t ej = nullptr;
+                if ((e = cudaEventCreateWithFlags(&ej, cudaEventDisableTiming)) != cudaSuccess ||
+                    (e = cudaEventRecord(ej, sc)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(st, ej, 0)) != cudaSuccess)
+                    return cuda_fail(e, "class join");
+                ev_join.push_back(ej);
+            }
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (cudaEvent_t ej : ev_join) cudaEventDestroy(ej);
     }
     if (count) {
         for (int i = 0; i < n; ++i) {
@@ -833,6 +895,8 @@ void bm_destroy(bm_ctx* ctx) {
     if (ctx->d_fault) cudaFree(ctx->d_fault);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    for (auto& kv : ctx->branches)
+        for (cudaStream_t s2 : kv.second) cudaStreamDestroy(s2);
     if (ctx->d_ring) cudaFree(ctx->d_ring);
     if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
     for (int b = 0; b < 2; ++b) {

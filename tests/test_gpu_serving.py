@@ -165,3 +165,36 @@ def test_autotuner_picks_a_configuration_with_identical_results(tmp_path, dt):
     assert np.array_equal(p_idx.cpu().numpy(), a_idx.cpu().numpy())
     for c in (plain, tuned, again):
         c.close()
+
+
+def test_mixed_class_batch_graph_replay():
+    """Several classes in one bm_match_batch: their launches run on parallel
+    branches of one captured graph.  Replays with new pixels give what each
+    job gives alone."""
+    ctx = B.Context(0)
+    st = torch.cuda.Stream()
+    specs = [(100, 90, 1, "f32", 8, 39, 3, 16), (64, 64, 1, "u8", 8, 21, 1, 16),
+             (80, 72, 4, "u8", 8, 39, 3, 32), (150, 133, 1, "f32", 7, 61, 4, 70),
+             (96, 96, 1, "u8", 7, 39, 4, 32)]
+    imgs, outs, reqs = [], [], []
+    for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
+        t = torch.from_numpy(_image(H, W, C, dt, 300 + i)).cuda()
+        o = ctx.outputs(t, p, s, K)
+        imgs.append(t)
+        outs.append(o)
+        reqs.append(ctx.request(t, p, win, s, K, o[0], o[1]))
+    torch.cuda.synchronize()
+    for rnd in range(2):
+        if rnd == 1:
+            for i, (t, (H, W, C, dt, p, win, s, K)) in enumerate(zip(imgs, specs)):
+                t.copy_(torch.from_numpy(_image(H, W, C, dt, 400 + i)))
+            torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            ctx.match_batch(reqs, stream=st)  # first call captures, then replays
+            ctx.match_batch(reqs, stream=st)
+        st.synchronize()
+        for (H, W, C, dt, p, win, s, K), t, o in zip(specs, imgs, outs):
+            a_idx, a_dist = ctx.match(t, p, win, s, K)
+            torch.cuda.synchronize()
+            assert torch.equal(a_idx, o[0]) and torch.equal(a_dist, o[1])
+    ctx.close()
