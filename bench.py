@@ -236,22 +236,25 @@ def run_reference(args, world, rank, dist):
 
 # ---------------------------------------------------------------- our arm
 
-def profiled_traffic(images_per_launch):
-    """DRAM bytes (read + write) per launch of the tensor-core kernel, from the
-    committed ncu summary (16-image capture scaled by images per launch, the
-    traffic being per image); None when the kernel source changed since."""
+def profiled_counters(images_per_launch):
+    """From the committed ncu summary of the tensor-core kernel (16-image
+    capture): DRAM bytes (read + write) per launch, scaled by images per
+    launch (the traffic is per image), and the tensor pipe's active
+    percentage; (None, None) when the kernel source changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "tc_match_kernel_512x512_f32_batch16.md")
     src = os.path.join(ROOT, "paper_2006_13714_gb300", "csrc", "selfconv_tc.cu")
     try:
         fields = dict(line.split(": ", 1) for line in open(path).read().splitlines()
-                      if line.startswith(("traffic_bytes_per_image:", "source_sha256_16:")))
+                      if line.startswith(("traffic_bytes_per_image:", "source_sha256_16:",
+                                          "tensor_pipe_active_pct:")))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if fields.get("source_sha256_16", "").strip() != digest:
-            return None
-        return float(fields["traffic_bytes_per_image"]) * images_per_launch
+            return None, None
+        pipe = float(fields["tensor_pipe_active_pct"]) if "tensor_pipe_active_pct" in fields else None
+        return float(fields["traffic_bytes_per_image"]) * images_per_launch, pipe
     except (OSError, KeyError, ValueError):
-        return None
+        return None, None
 
 
 def serve_stream(ctx, pkg, synth, dev, n=2000, seed=SEED_BASE + 55, side=2048):
@@ -773,7 +776,7 @@ def run_ours(args, world, rank, local, dist):
     peak_src = "of measured (bf16 sustained)"
     if peak is None:
         peak, peak_src = 1700.0, "of fallback (bf16 sustained)"
-    traffic = profiled_traffic(imgs_per_launch)
+    traffic, pipe_pct = profiled_counters(imgs_per_launch)
     stage_share = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in tm.values())), 4)
                    for k, v in tm.items() if v["launches"]}
 
@@ -867,7 +870,10 @@ def run_ours(args, world, rank, local, dist):
                      "algorithmic_flop_per_launch": flop_per_launch,
                      "issued_flop_per_launch": issued_per_launch,
                      "issued_frac": issued_per_launch / (tc_ms / 1e3) / 1e12 / peak,
-                     "images_per_launch": imgs_per_launch},
+                     "images_per_launch": imgs_per_launch,
+                     "tensor_pipe_active_ncu": pipe_pct,
+                     "tensor_pipe_note": "sm__pipe_tensor_cycles_active (pct of peak, active) of one "
+                                         "16-image launch, ncu; issued MMAs, not the algorithmic fraction"},
         "cpu_baseline": cpu,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
