@@ -226,6 +226,21 @@ __device__ __forceinline__ void tmem_ld_blocks<1>(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same 16 columns with their maximum per lane (tcgen05.ld.red: the
+// load and the reduction in one instruction).
+__device__ __forceinline__ void tmem_ld_max(uint32_t taddr, float* v, float& vmax) {
+    uint32_t r[16], m;
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(m)
+        : "r"(taddr + 0u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    vmax = __uint_as_float(m);
+}
+
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
 // LBO = byte step between K-adjacent core matrices, SBO = between M/N-adjacent.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -1005,8 +1020,13 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     const uint32_t colbase = tmem_base + lane_base + (2 * k + buf) * G.bufcols +
                                              jl * G.Rb + 16 * b0;
                     for (int bb = 0; bb < nblk; ++bb) {
-                        float w[16];
-                        tmem_ld_blocks<1>(colbase + 16 * bb, w);
+                        float w[16], wmax;
+                        tmem_ld_max(colbase + 16 * bb, w, wmax);
+                        // a block whose values all fall below every lane's threshold
+                        // adds nothing: skipped on the load's own maximum (which also
+                        // covers rows outside a lane's window -- a false positive
+                        // only costs the full test below)
+                        if (!__any_sync(0xffffffffu, xok && wmax >= thr)) continue;
                         const int b = b0 + bb;
                         // this lane's valid rows of block b: [max(i0, 0), min(i1, 15)]
                         const int i0 = max(lo - 16 * b, 0), i1 = min(hi - 16 * b, 15);
