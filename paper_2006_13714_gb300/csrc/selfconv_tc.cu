@@ -85,6 +85,7 @@ struct TcGeom {
     int qpitch, plane_stage, stage_bytes;
     int f32;
     int a_bytes;
+    int ts, a_cols;           // A operand in tensor memory (TS MMAs): columns per slot (0: SS)
     int off_base, off_a, off_stage, off_buf, slot_bytes;  // inside a slot's region
     int off_slots, off_an, off_heap, off_bar, smem_total;
 };
@@ -204,6 +205,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+// The same with A in tensor memory (a_taddr: its first column, lane 0).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a_taddr, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+        "r"(a_taddr), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 4 consecutive 32-bit columns of the warp's 32 lanes (one value per lane and column).
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
@@ -730,6 +747,46 @@ __device__ __forceinline__ void form_A(const TcGeom& G, const TileInfo& T, const
     }
 }
 
+// A in tensor memory, for the TS form of the MMAs (classes whose A operand
+// does not fit in shared memory beside the staged tile): each epilogue lane
+// writes its own row (TMEM lane m = A row m = reference m of the tile), the
+// K elements two per 32-bit column -- 16-byte chunk kc of plane pl at
+// columns a_row + (pl * nkc + kc) * 4.  The same values as form_A.
+template <bool kF32>
+__device__ __forceinline__ void form_A_tmem(const TcGeom& G, const TileInfo& T, const TcJob& J,
+                                            const uint8_t* sbase, int delta, uint32_t a_row, int m) {
+    constexpr int nplanes = kF32 ? 2 : 1;
+    const int mw = m >> 5, ml = m & 31;
+    const int ry = T.ry0 + (mw / G.wgx) * G.rr + ml / G.rc;
+    const int rx = T.rx0 + (mw % G.wgx) * G.rc + ml % G.rc;
+    const bool ok = ry < J.n_ry && rx < J.n_rx;
+    for (int pl = 0; pl < nplanes; ++pl) {
+        for (int kc = 0; kc < G.nkc; ++kc) {  // warp-uniform: every lane stores every chunk
+            const int u = kc / G.pw, q = kc - u * G.pw;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (ok && u < G.p) {
+                const uint8_t* row = sbase + pl * G.base_bytes + (ry * G.s - T.Y0 + u) * G.base_pitch;
+                v = lds_shifted16(row, delta + (rx * G.s - T.X0) * G.Cp + 8 * q);
+                const int valid = G.p * G.Cp - 8 * q;
+                uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (2 * i >= valid) w[i] = 0;
+                    else if (2 * i + 1 >= valid) w[i] &= 0xffffu;
+                    if (!kF32) {
+                        const float lo_f = 2.0f * bf16_val((uint16_t)(w[i] & 0xffffu));
+                        const float hi_f = 2.0f * bf16_val((uint16_t)(w[i] >> 16));
+                        w[i] = (uint32_t)bf16_bits(lo_f) | ((uint32_t)bf16_bits(hi_f) << 16);
+                    }
+                }
+                v = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            tmem_st4(a_row + (uint32_t)((pl * G.nkc + kc) * 4), v);
+        }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- the kernel
 //
 // Persistent: CTA b walks the tiles b, b + G, b + 2G, ... of every job of
@@ -831,8 +888,9 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             if (ok) ok = __all_sync(0xffffffffu, mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6));
             if (!ok) break;
             base_pending = -1;
-            // (3) this warp's share of A (the slot's epilogue warps form the rest)
-            form_A<kF32>(G, T, J, sbase, sa, delta, 128 + lane, 160);
+            // (3) this warp's share of A (the slot's epilogue warps form the rest;
+            // with A in tensor memory they form all of it)
+            if (!G.ts) form_A<kF32>(G, T, J, sbase, sa, delta, 128 + lane, 160);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(BAR(k, kBarAFull));
@@ -897,6 +955,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             const uint64_t da_hi = sdesc(smem_u32(slot + G.off_a), 128, sbo_a);
             const uint64_t da_lo = da_hi + (uint64_t)(G.a_bytes >> 4);
             const uint64_t dn_a = sdesc(an, 128, 256);
+            const uint32_t ta_hi = tmem_base + (uint32_t)(2 * NS * G.bufcols + k * G.a_cols);  // TS
             int cs = 0;
             bool ok = true;
             for (int turn = 0; ok; ++turn) {
@@ -928,12 +987,22 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     for (int kc = 0; kc < G.nkc; kc += 2) {
                         const uint64_t oa = (uint64_t)(kc * 8);  // kc * 128 bytes
                         const uint64_t ob = (uint64_t)((qq * G.qpitch + u * 16) >> 4);
-                        mma_bf16(d, da_hi + oa, db_hi + ob, idesc, acc);
-                        acc = 1;
-                        if (kF32) {
-                            mma_bf16(d, da_hi + oa, db_lo + ob, idesc, 1);
-                            mma_bf16(d, da_lo + oa, db_hi + ob, idesc, 1);
+                        if (G.ts) {
+                            // A in tensor memory: K chunks kc, kc + 1 at columns 4 kc ..
+                            const uint32_t ta = ta_hi + (uint32_t)(kc * 4);
+                            mma_bf16_ts(d, ta, db_hi + ob, idesc, acc);
+                            if (kF32) {
+                                mma_bf16_ts(d, ta, db_lo + ob, idesc, 1);
+                                mma_bf16_ts(d, ta + (uint32_t)(G.nkc * 4), db_hi + ob, idesc, 1);
+                            }
+                        } else {
+                            mma_bf16(d, da_hi + oa, db_hi + ob, idesc, acc);
+                            if (kF32) {
+                                mma_bf16(d, da_hi + oa, db_lo + ob, idesc, 1);
+                                mma_bf16(d, da_lo + oa, db_hi + ob, idesc, 1);
+                            }
                         }
+                        acc = 1;
                         // next pair of 16-byte K chunks: (u, q) advances by two in row-major order
                         qq += 2;
                         while (qq >= G.pw) { qq -= G.pw; ++u; }
@@ -990,13 +1059,21 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             // the slot's A operand (with the producer): the A region is free
             // once the previous tile's MMAs are done, the staged tile has landed
             if (turn > 0 && !mbar_wait(BAR(k, kBarAEmpty), (turn - 1) & 1, abort_flag, 5)) break;
+            tc_fence_after();
             if (!mbar_wait(BAR(k, kBarBase), turn & 1, abort_flag, 6)) break;
             {
                 const int e0 = (T.X0 * G.Cp) & ~7;
-                form_A<kF32>(G, T, J, smem + G.off_slots + k * G.slot_bytes + G.off_base,
-                             smem + G.off_slots + k * G.slot_bytes + G.off_a, T.X0 * G.Cp - e0,
-                             threadIdx.x & 127, 160);
+                if (G.ts)
+                    form_A_tmem<kF32>(G, T, J, smem + G.off_slots + k * G.slot_bytes + G.off_base,
+                                      T.X0 * G.Cp - e0,
+                                      tmem_base + lane_base + (uint32_t)(2 * NS * G.bufcols + k * G.a_cols),
+                                      threadIdx.x & 127);
+                else
+                    form_A<kF32>(G, T, J, smem + G.off_slots + k * G.slot_bytes + G.off_base,
+                                 smem + G.off_slots + k * G.slot_bytes + G.off_a, T.X0 * G.Cp - e0,
+                                 threadIdx.x & 127, 160);
                 fence_proxy_async();
+                tc_fence_before();  // tensor-memory A: its stores before the MMAs
                 __syncwarp();
                 if (lane == 0) mbar_arrive(BAR(k, kBarAFull));
             }
@@ -1183,9 +1260,15 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     // lane -> reference mapping: rr reference rows x rc columns per warp, a
     // wgy x wgx grid of 4 warps
     static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
+    // A in shared memory first; classes where nothing fits (the staged tile
+    // plus A beyond 227 KB: float32 with four channels, large windows) keep
+    // A in tensor memory instead (TS MMAs), beside narrower accumulators
+    for (int ts = 0; ts <= 1; ++ts)
     for (int ns = 2; ns >= 1; --ns) {
         if (ns == 2 && t.HL > 32) continue;
-        const int bufcols = kTmemCols / (2 * ns);
+        const int a_cols = ts ? nplanes * t.nkc * 4 : 0;  // 16-bit elements, two per column
+        const int bufcols = ((kTmemCols - ns * a_cols) / (2 * ns)) / 16 * 16;
+        if (bufcols < 16) continue;
         bool found = false;
         long long best = 0;
         TcGeom bestc{};
@@ -1214,7 +1297,9 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
                     c.qpitch = (c.kcols * c.Rb + g.p_eff + 16) * 16;
                     c.plane_stage = c.pw * c.qpitch;
                     c.stage_bytes = (nplanes * c.plane_stage + c.kcols * c.Rb * 16 + 127) / 128 * 128;
-                    c.a_bytes = 128 * c.nkc * 16;
+                    c.ts = ts;
+                    c.a_cols = a_cols;
+                    c.a_bytes = ts ? 0 : 128 * c.nkc * 16;
                     // one slot: staged tile, A, stages, append buffers
                     int off = 0;
                     c.off_base = off; off += (nplanes * c.base_bytes + 1023) / 1024 * 1024;

@@ -224,6 +224,28 @@ def test_window_split_equals_unsplit(ctx, case):
     compare(img0, p, win, s, K, a_idx.cpu().numpy(), a_dist.cpu().numpy())
 
 
+TS_CASES = [
+    # classes whose A operand lives in tensor memory (TS MMAs): the staged tile
+    # plus a shared-memory A does not fit
+    ("ts_f32_c4_p8", 96, 90, 4, "f32", 8, 39, 3, 16),
+    ("ts_f32_c4_p7", 101, 93, 4, "f32", 7, 39, 4, 16),
+    ("ts_u8_c4_p8_k70", 110, 97, 4, "u8", 8, 61, 3, 70),
+    ("ts_u8_c4_p7_k70", 90, 99, 4, "u8", 7, 39, 4, 70),
+]
+
+
+@pytest.mark.parametrize("case", TS_CASES, ids=[c[0] for c in TS_CASES])
+def test_tensor_memory_a_classes(ctx, case):
+    name, H, W, C, dt, p, win, s, K = case
+    code = B.BM_U8 if dt == "u8" else B.BM_F32
+    assert B.bm_workspace_bytes(H, W, C, code, p, win, s, K) > 0  # the tensor-core path
+    img = make_image(H, W, C, dt, seed=zlib.crc32(name.encode()) % 10007, sigma=20.0)
+    before = ctx.stats()["tc_jobs"]
+    gidx, gdist = run(ctx, img, p, win, s, K, "selfconv")
+    assert ctx.stats()["tc_jobs"] == before + 1
+    compare(img, p, win, s, K, gidx, gdist, threads=0)
+
+
 def test_selfconv_equals_direct_bitwise_on_u8(ctx):
     img = make_image(200, 180, 1, "u8", seed=5)
     a = run(ctx, img, 8, 39, 3, 16, "selfconv")
