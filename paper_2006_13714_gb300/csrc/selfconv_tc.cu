@@ -984,28 +984,34 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     const uint64_t db_lo = db_hi + (uint64_t)(G.plane_stage >> 4);
                     uint32_t acc = 0;
                     int u = 0, qq = 0;
-                    for (int kc = 0; kc < G.nkc; kc += 2) {
-                        const uint64_t oa = (uint64_t)(kc * 8);  // kc * 128 bytes
-                        const uint64_t ob = (uint64_t)((qq * G.qpitch + u * 16) >> 4);
-                        if (G.ts) {
-                            // A in tensor memory: K chunks kc, kc + 1 at columns 4 kc ..
+                    if (G.ts) {
+                        // A in tensor memory: K chunks kc, kc + 1 at columns 4 kc ..
+                        for (int kc = 0; kc < G.nkc; kc += 2) {
+                            const uint64_t ob = (uint64_t)((qq * G.qpitch + u * 16) >> 4);
                             const uint32_t ta = ta_hi + (uint32_t)(kc * 4);
                             mma_bf16_ts(d, ta, db_hi + ob, idesc, acc);
+                            acc = 1;
                             if (kF32) {
                                 mma_bf16_ts(d, ta, db_lo + ob, idesc, 1);
                                 mma_bf16_ts(d, ta + (uint32_t)(G.nkc * 4), db_hi + ob, idesc, 1);
                             }
-                        } else {
+                            qq += 2;
+                            while (qq >= G.pw) { qq -= G.pw; ++u; }
+                        }
+                    } else {
+                        for (int kc = 0; kc < G.nkc; kc += 2) {
+                            const uint64_t oa = (uint64_t)(kc * 8);  // kc * 128 bytes
+                            const uint64_t ob = (uint64_t)((qq * G.qpitch + u * 16) >> 4);
                             mma_bf16(d, da_hi + oa, db_hi + ob, idesc, acc);
+                            acc = 1;
                             if (kF32) {
                                 mma_bf16(d, da_hi + oa, db_lo + ob, idesc, 1);
                                 mma_bf16(d, da_lo + oa, db_hi + ob, idesc, 1);
                             }
+                            // next pair of 16-byte K chunks: (u, q) advances by two in row-major order
+                            qq += 2;
+                            while (qq >= G.pw) { qq -= G.pw; ++u; }
                         }
-                        acc = 1;
-                        // next pair of 16-byte K chunks: (u, q) advances by two in row-major order
-                        qq += 2;
-                        while (qq >= G.pw) { qq -= G.pw; ++u; }
                     }
                     mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
                     mma_commit(BAR(k, kBarSEmpty + stage));
