@@ -55,7 +55,7 @@ constexpr int kTileWarps = 8;
 constexpr int kMaxTileRefs = 64;
 constexpr int kCandCap = kFbSlots * 32;  // window keys kept per overflow reference
 constexpr int kMaxRerankJobs = 64;
-constexpr int kTileSmemLimit = 160 * 1024;
+constexpr int kTileSmemLimit = 220 * 1024;  // within the 227 KB a block may use
 
 struct RerankJob {
     const float* img;
