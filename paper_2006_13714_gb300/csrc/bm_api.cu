@@ -275,7 +275,7 @@ cudaError_t timed(bm_ctx* ctx, int stage, cudaStream_t st, F&& launch, const int
 
 std::string class_key(const Geom& g) {
     std::ostringstream o;
-    o << "dtype" << g.dtype << "_C" << g.C << "_p" << g.p << "_w" << (2 * g.h + 1) << "_s" << g.s
+    o << "tc2_dtype" << g.dtype << "_C" << g.C << "_p" << g.p << "_w" << (2 * g.h + 1) << "_s" << g.s
       << "_K" << g.K;
     return o.str();
 }

@@ -116,6 +116,7 @@ constexpr int kMaxJobs = 64;  // jobs per launch (kept inline in the kernel para
 // alone, 171 tiles, ran 20 % slower split in two).
 constexpr int kSplitTarget = 152;
 constexpr int kMaxSplit = 4;
+constexpr int kSplitChoices = 3;  // tuner: 1, 2 or 4 parts
 
 struct TcParams {
     TcGeom g;
@@ -1520,10 +1521,13 @@ bool tc_supported(const Geom& g) {
     return make_tc_geom(g, t);
 }
 
+// Tuner choices: every fitting tile configuration (make_tc_geom's
+// candidates) times kSplitChoices window splits (1, 2 or 4 parts, bounded by
+// the job's part-list room): choice = configuration * kSplitChoices + s.
 int tc_num_choices(const Geom& g) {
     TcGeom t{};
     int n = 0;
-    return make_tc_geom(g, t, -1, &n) ? n : 0;
+    return make_tc_geom(g, t, -1, &n) ? n * kSplitChoices : 0;
 }
 
 int tc_score_bits(const Geom& g) {
@@ -1549,7 +1553,10 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
         static thread_local TcParams P;
         P = TcParams{};
         const int choice = choices ? choices[i] : -1;
-        if (!make_tc_geom(gs[i], P.g, choice)) return cudaErrorNotSupported;
+        // an explicit choice fixes the tile configuration and the split
+        const int gchoice = choice >= 0 ? choice / kSplitChoices : -1;
+        const int wsel = choice >= 0 ? 1 << (choice % kSplitChoices) : 0;  // 0: heuristic
+        if (!make_tc_geom(gs[i], P.g, gchoice)) return cudaErrorNotSupported;
         P.fault = as[i].fault;
         P.inject = as[i].inject;
         int tiles = 0, nj = 0;
@@ -1561,9 +1568,10 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
             ++nj;
             ++i;
         }
-        // window split: only when the launch's tiles leave SMs idle, and then
-        // for every job that has part lists (wsplit of its arguments)
-        const bool split = tiles < kSplitTarget;
+        // window split: by the heuristic only when the launch's tiles leave
+        // SMs idle, then for every job that has part lists (wsplit of its
+        // arguments); a tuned choice sets the parts itself
+        const bool split = wsel > 0 || tiles < kSplitTarget;
         MergeParams M{};
         M.N = P.g.f32 ? P.g.HL : P.g.K;
         M.f32 = P.g.f32;
@@ -1573,7 +1581,8 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
             TcJob& J = P.jobs[j];
             J.tile_begin = tiles;
             const int jt = J.tiles_x * ((J.n_ry + P.g.ty - 1) / P.g.ty);
-            const int w = (split && a.split_idx && a.split_val) ? split_cap(gs[first + j], P.g, a.wsplit) : 1;
+            const int room = (a.split_idx && a.split_val) ? a.wsplit : 1;
+            const int w = split ? split_cap(gs[first + j], P.g, wsel > 0 ? std::min(wsel, room) : room) : 1;
             if (w > 1) {
                 J.wsplit = w;
                 MergeJob& m = M.jobs[M.njobs++];

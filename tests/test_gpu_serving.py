@@ -157,7 +157,7 @@ def test_autotuner_picks_a_configuration_with_identical_results(tmp_path, dt):
     assert np.array_equal(p_idx.cpu().numpy(), t_idx.cpu().numpy())
     assert np.array_equal(p_dist.cpu().numpy(), t_dist.cpu().numpy())
     lines = open(cache).read().split("\n")
-    assert any(line.startswith("dtype") for line in lines)
+    assert any(line.startswith("tc2_dtype") for line in lines)
     # a second context reads the table instead of tuning again
     again = B.Context(0, tune_cache=cache)
     a_idx, a_dist = again.match(t, 8, 39, 3, 16)
@@ -198,3 +198,25 @@ def test_mixed_class_batch_graph_replay():
             torch.cuda.synchronize()
             assert torch.equal(a_idx, o[0]) and torch.equal(a_dist, o[1])
     ctx.close()
+
+
+def test_autotuner_window_split_choice_is_exact(tmp_path):
+    """The tuner's choices include the window split (1, 2 or 4 parts); a job
+    that splits alone gets a recorded pick whose results equal the
+    heuristic's, for uint8 (exact) and float32 (pool re-ranked)."""
+    cache = str(tmp_path / "tune.txt")
+    for dt in ("u8", "f32"):
+        img = _image(96, 90, 1, dt, 45)
+        code = B.BM_U8 if dt == "u8" else B.BM_F32
+        assert B.bm_window_split(96, 90, 1, code, 8, 39, 3, 16) > 1
+        t = torch.from_numpy(img).cuda()
+        plain = B.Context(0)
+        p_idx, p_dist = plain.match(t, 8, 39, 3, 16)
+        tuned = B.Context(0, tune_cache=cache)
+        t_idx, t_dist = tuned.match(t, 8, 39, 3, 16)
+        torch.cuda.synchronize()
+        assert torch.equal(p_idx, t_idx) and torch.equal(p_dist, t_dist)
+        for c in (plain, tuned):
+            c.close()
+    picks = [ln.split() for ln in open(cache).read().split("\n") if ln.strip()]
+    assert len(picks) == 2 and all(int(p[1]) >= -1 for p in picks)
