@@ -583,10 +583,25 @@ def ncc_throughput(ctx, imgs, stream, dev, pairs, n=16):
         if rep:
             times.append(e0.elapsed_time(e1) / n)
     ms = min(times)
+    # the same on uint8 stand-ins (the tensor-core form: exact cross terms on
+    # tcgen05, a pool of 32 ranked exactly)
+    u8 = [torch.clamp(imgs[i], 0, 255).round().to(torch.uint8).contiguous() for i in range(n)]
+    times8 = []
+    for rep in range(3):
+        e0.record(stream)
+        for i in range(n):
+            ctx.match_ncc(u8[i], p, win, s, K, out=outs[i], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rep:
+            times8.append(e0.elapsed_time(e1) / n)
+    ms8 = min(times8)
     flop = 2.0 * pairs * p * p + 2.0 * (H - p + 1) * (W - p + 1) * p * p
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = flop / (ms / 1e3) / 1e12
     return {"images": n, "us_per_image": 1e3 * ms, "ref_patches_per_s": ny * nx / (ms / 1e3),
+            "uint8_tensor_core": {"us_per_image": 1e3 * ms8, "ref_patches_per_s": ny * nx / (ms8 / 1e3),
+                                  "useful_tmac_per_s": pairs * p * p / (ms8 / 1e3) / 1e12},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          "peak_source": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2.07 GHz)",

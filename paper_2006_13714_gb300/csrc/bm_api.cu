@@ -627,6 +627,13 @@ int get_stream_ws(bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out) {
 
 namespace bm {
 int ctx_device(const ::bm_ctx* ctx) { return ctx->device; }
+int ctx_workspace(::bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out) {
+    return get_stream_ws(ctx, st, bytes, out);
+}
+int* ctx_fault_word(::bm_ctx* ctx) { return ctx->d_fault; }
+unsigned long long* ctx_counters(::bm_ctx* ctx) { return ctx->d_counters; }
+void ctx_count_tc_job(::bm_ctx* ctx) { ctx->tc_jobs += 1; }
+bool ctx_uses_tc(::bm_ctx* ctx) { return ctx->algo != BM_ALGO_DIRECT; }
 }  // namespace bm
 
 namespace {

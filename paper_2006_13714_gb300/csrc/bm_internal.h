@@ -62,6 +62,16 @@ __device__ __forceinline__ void warp_list_offer(unsigned long long key, unsigned
 
 // Device ordinal of a context (bm_api.cu).
 int ctx_device(const ::bm_ctx* ctx);
+// For entry points in other files (bm_api.cu): the per-stream workspace of
+// at least `bytes` (budget-checked, stream-ordered), the sticky timeout
+// word, the device counters ([0] overflow, [1] fp64 rechecks, [2] bound
+// violations), the tensor-core job counter, and whether the context's
+// algorithm allows the tensor-core path.
+int ctx_workspace(::bm_ctx* ctx, cudaStream_t st, size_t bytes, void** out);
+int* ctx_fault_word(::bm_ctx* ctx);
+unsigned long long* ctx_counters(::bm_ctx* ctx);
+void ctx_count_tc_job(::bm_ctx* ctx);
+bool ctx_uses_tc(::bm_ctx* ctx);
 
 constexpr int kMaxK = 128;        // largest K served
 constexpr int kMaxPatchElems = 256;  // p*p*C limit of every kernel
@@ -82,6 +92,10 @@ struct Geom {
     int plane_pitch;     // elements per plane row (multiple of 8)
     int plane_rows;      // rows per plane (H + padding)
     int L;               // float32 candidate pool per reference
+    // normalized cross-correlation (bm_match_ncc on tensor cores): uncentred
+    // operands, no norm K-step, scores a_j / ||X_j|| in the epilogue, a pool
+    // of L for both dtypes (set by the NCC entry point after make_geom)
+    int ncc = 0;
 };
 
 // Fill g from the arguments; returns 0 or a negative bm_status.
@@ -105,6 +119,10 @@ struct PrepJob {
     void* nrm;                // norms [Hc][Wc]
     uint16_t* nsp;            // nullable: split norms [Wc][Hc][8]
     int H, W, C, Cp, p, Hc, Wc, plane_pitch, plane_rows, dtype;
+    // NCC: uncentred planes (uint8 too gets a zero lo plane), uncentred norms,
+    // and nsp holding 1 / ||X_j|| (float, first 4 bytes of each 16) instead of
+    // the split norm pieces
+    int ncc = 0;
 };
 PrepJob make_prep_job(const Geom& g, const void* img, float* center, uint16_t* plane0,
                       uint16_t* plane1, void* nrm, uint16_t* nsp);

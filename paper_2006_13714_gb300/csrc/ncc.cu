@@ -396,6 +396,204 @@ __global__ void __launch_bounds__(256) ncc_warp_kernel(const NccParams Q) {
     }
 }
 
+
+// ---------------------------------------------------------------- tensor-core form
+
+// The tensor-core kernel in its NCC mode (uncentred operands, no norm K-step,
+// each value scaled by 1 / ||X_j|| in the epilogue) leaves per reference a
+// pool of the L best approximate scores s~_j = a~_j / ||X_j|| (a~_j the
+// tensor-core cross term: exact for uint8, the bf16 hi/lo split for float32,
+// |a~_j - a_j| <= eps ||X_r|| ||X_j||; 32-bit pool keys round s~ up by less
+// than round_rel relative).  This kernel ranks the pool exactly -- uint8
+// through (a, n) integer products as the CUDA-core kernels do, float32 by the
+// float32 score of a direct cross term -- and keeps the pool's top K when no
+// candidate outside it can reach them: the K-th exact pool score must exceed
+// the pool's last approximate score plus the estimate's error bound.  Else
+// (or when the pool is full of ties) the reference's whole window is ranked
+// directly.  One warp per reference.
+
+struct NccPoolParams {
+    const void* img;
+    const void* nrm;          // uncentred norms [Hc][Wc] (uint8: int32, float32: float)
+    const int32_t* pool_idx;  // [nR][L], best first
+    const float* pool_score;
+    int32_t* out_idx;
+    float* out_score;
+    unsigned long long* counters;  // [0] overflow
+    int H, W, C, p, h, s, K, L, n_ry, n_rx, Hc, Wc, u8;
+    float eps;                // float32 cross-term bound (relative to ||X_r|| ||X_j||)
+    float round_rel;          // pool-score rounding (relative)
+};
+
+// Exact (uint8) or float32 cross term <X_r, X_j> and ||X_j||^2 from global memory.
+template <bool kU8>
+__device__ __forceinline__ float cross_term(const NccPoolParams& Q, int yr, int xr, int yc, int xc) {
+    const int pc = Q.p * Q.C;
+    float a = 0.f;
+    for (int u = 0; u < Q.p; ++u) {
+        const size_t r0 = ((size_t)(yr + u) * Q.W + xr) * Q.C, c0 = ((size_t)(yc + u) * Q.W + xc) * Q.C;
+        for (int e = 0; e < pc; ++e) {
+            float x, y;
+            if (kU8) {
+                x = __ldg(static_cast<const uint8_t*>(Q.img) + r0 + e);
+                y = __ldg(static_cast<const uint8_t*>(Q.img) + c0 + e);
+            } else {
+                x = __ldg(static_cast<const float*>(Q.img) + r0 + e);
+                y = __ldg(static_cast<const float*>(Q.img) + c0 + e);
+            }
+            a = fmaf(x, y, a);
+        }
+    }
+    return a;
+}
+
+__device__ __forceinline__ float norm_at(const NccPoolParams& Q, bool u8, int y, int x) {
+    const size_t o = (size_t)y * Q.Wc + x;
+    return u8 ? (float)__ldg(static_cast<const int*>(Q.nrm) + o) : __ldg(static_cast<const float*>(Q.nrm) + o);
+}
+
+// float32 key: smaller is better (complemented order-preserving score bits above the offset)
+__device__ __forceinline__ unsigned long long score_key(float sc, int off) {
+    sc += 0.f;  // -0 -> +0
+    const unsigned b = __float_as_uint(sc);
+    const unsigned ord = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ((unsigned long long)~ord << 32) | (unsigned)off;
+}
+__device__ __forceinline__ float key_score(unsigned long long k) {
+    const unsigned ord = ~(unsigned)(k >> 32);
+    return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7fffffffu) : ~ord);
+}
+
+// uint8: entry c offered to the warp's exact list (lane i = rank i < K).
+__device__ __forceinline__ void ent_list_offer(const Ent& c, Ent& mine, Ent& kth, int lane, int K) {
+    unsigned mask = __ballot_sync(0xffffffffu, c.off >= 0 && better<true>(c, kth));
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        Ent b;
+        b.a = __shfl_sync(0xffffffffu, c.a, src);
+        b.n = __shfl_sync(0xffffffffu, c.n, src);
+        b.off = __shfl_sync(0xffffffffu, c.off, src);
+        if (!better<true>(b, kth)) continue;  // the K-th moved past it
+        const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && better<true>(mine, b)));
+        Ent up;
+        up.a = __shfl_up_sync(0xffffffffu, mine.a, 1);
+        up.n = __shfl_up_sync(0xffffffffu, mine.n, 1);
+        up.off = __shfl_up_sync(0xffffffffu, mine.off, 1);
+        if (lane == pos) mine = b;
+        else if (lane > pos) mine = up;
+        kth.a = __shfl_sync(0xffffffffu, mine.a, K - 1);
+        kth.n = __shfl_sync(0xffffffffu, mine.n, K - 1);
+        kth.off = __shfl_sync(0xffffffffu, mine.off, K - 1);
+    }
+}
+
+template <bool kU8>
+__global__ void __launch_bounds__(128) ncc_pool_kernel(const __grid_constant__ NccPoolParams Q) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t r = (size_t)blockIdx.x * 4 + warp;
+    if (r >= (size_t)Q.n_ry * Q.n_rx) return;  // whole warp
+    const int ry = (int)(r / Q.n_rx), rx = (int)(r % Q.n_rx);
+    const int yr = ry * Q.s, xr = rx * Q.s;
+    const float nr = norm_at(Q, kU8, yr, xr);
+    const int K = Q.K;
+    // the pool, in order; entry L - 1 present means the pool is full
+    Ent mine{0.f, 1.f, -1}, kth{0.f, 1.f, -1};
+    unsigned long long mk = ~0ull, kk = ~0ull;
+    bool full = false;
+    float last = 0.f;  // the pool's last (worst) approximate score, rounded up
+    for (int i0 = 0; i0 < Q.L; i0 += 32) {
+        const int i = i0 + lane;
+        const int off = i < Q.L ? __ldg(Q.pool_idx + r * Q.L + i) : -1;
+        if (i == Q.L - 1 && off >= 0) {
+            full = true;
+            last = __ldg(Q.pool_score + r * Q.L + i);
+        }
+        int yc = 0, xc = 0;
+        float a = 0.f, n = 1.f;
+        if (off >= 0) {
+            yc = off / Q.W;
+            xc = off - yc * Q.W;
+            a = cross_term<kU8>(Q, yr, xr, yc, xc);
+            n = norm_at(Q, kU8, yc, xc);
+        }
+        if (kU8) {
+            Ent c{0.f, 1.f, off};
+            if (off >= 0 && n != 0.f && nr != 0.f) {
+                c.a = a;
+                c.n = n;
+            }
+            ent_list_offer(c, mine, kth, lane, K);
+        } else {
+            const unsigned long long key =
+                off >= 0 ? score_key((n > 0.f && nr > 0.f) ? a * rsqrtf(n) : 0.f, off) : ~0ull;
+            warp_list_offer(key, mk, kk, lane, K);
+        }
+    }
+    full = __any_sync(0xffffffffu, full);
+    last = __shfl_sync(0xffffffffu, last, (Q.L - 1) & 31);
+    // can a candidate outside the pool reach the exact top K?
+    bool overflow = false;
+    if (full) {
+        // outside candidates: approximate score <= last, exact score <= last + bound
+        if (kU8) {
+            const double sK = kth.off < 0 ? -1.0 : (kth.n > 0.f ? (double)kth.a / sqrt((double)kth.n) : 0.0);
+            const double lim = (double)last * (1.0 + 2.0 * Q.round_rel) + fabs((double)last) * 1e-6 + 1e-30;
+            overflow = !(sK > lim);
+        } else {
+            const float sK = kk == ~0ull ? -__int_as_float(0x7f800000) : key_score(kk);
+            const float bound = Q.eps * sqrtf(fmaxf(nr, 0.f)) + fabsf(last) * 1e-5f + 1e-30f;
+            overflow = !(sK > last + bound);
+        }
+    }
+    if (overflow) {
+        if (lane == 0) atomicAdd(Q.counters, 1ull);
+        // the whole window, directly
+        mine = Ent{0.f, 1.f, -1};
+        kth = Ent{0.f, 1.f, -1};
+        mk = kk = ~0ull;
+        const int cy0 = max(0, yr - Q.h), cy1 = min(Q.Hc - 1, yr + Q.h);
+        const int cx0 = max(0, xr - Q.h), cx1 = min(Q.Wc - 1, xr + Q.h);
+        const int wx = cx1 - cx0 + 1, total = (cy1 - cy0 + 1) * wx;
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            int off = -1;
+            float a = 0.f, n = 1.f;
+            if (j < total) {
+                const int yc = cy0 + j / wx, xc = cx0 + j % wx;
+                off = yc * Q.W + xc;
+                a = cross_term<kU8>(Q, yr, xr, yc, xc);
+                n = norm_at(Q, kU8, yc, xc);
+            }
+            if (kU8) {
+                Ent c{0.f, 1.f, off};
+                if (off >= 0 && n != 0.f && nr != 0.f) {
+                    c.a = a;
+                    c.n = n;
+                }
+                ent_list_offer(c, mine, kth, lane, K);
+            } else {
+                const unsigned long long key =
+                    off >= 0 ? score_key((n > 0.f && nr > 0.f) ? a * rsqrtf(n) : 0.f, off) : ~0ull;
+                warp_list_offer(key, mk, kk, lane, K);
+            }
+        }
+    }
+    if (lane < K) {
+        float sc = -__int_as_float(0x7f800000);
+        int off = -1;
+        if (kU8) {
+            off = mine.off;
+            if (off >= 0) sc = nr > 0.f ? (float)((double)mine.a / sqrt((double)nr * (double)mine.n)) : 0.f;
+        } else if (mk != ~0ull) {
+            off = (int)(unsigned)mk;
+            sc = nr > 0.f ? key_score(mk) * rsqrtf(nr) : 0.f;
+        }
+        Q.out_idx[r * K + lane] = off;
+        Q.out_score[r * K + lane] = sc;
+    }
+}
+
 using NccKernel = void (*)(NccParams);
 
 NccKernel pick_fast(int p, int C, bool u8) {
@@ -423,6 +621,63 @@ struct DevGuard {
     }
 };
 
+
+// The tensor-core form: uncentred planes and norms (1 / ||X_j|| in the
+// split-norm slots), the tensor-core kernel in its NCC mode writing a pool of
+// L per reference, then ncc_pool_kernel.  Workspace from the context.
+int ncc_tensor_core(bm_ctx* ctx, const Geom& g, const void* img, int32_t* out_idx, float* out_score,
+                    cudaStream_t st) {
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t b_plane = al(plane_bytes(g)), b_nrm = al(nrm_bytes(g)), b_nsp = al(nsp_bytes(g));
+    const size_t b_pool = al((size_t)g.nR * g.L * 4);
+    const size_t total = 2 * b_plane + b_nrm + b_nsp + 2 * b_pool + 256;
+    void* ws = nullptr;
+    int rc = ctx_workspace(ctx, st, total, &ws);
+    if (rc != BM_OK) return rc;
+    char* b = static_cast<char*>(ws);
+    uint16_t* p0 = reinterpret_cast<uint16_t*>(b);
+    uint16_t* p1 = reinterpret_cast<uint16_t*>(b + b_plane);
+    void* nrm = b + 2 * b_plane;
+    uint16_t* nsp = reinterpret_cast<uint16_t*>(b + 2 * b_plane + b_nrm);
+    int32_t* pidx = reinterpret_cast<int32_t*>(b + 2 * b_plane + b_nrm + b_nsp);
+    float* pscore = reinterpret_cast<float*>(b + 2 * b_plane + b_nrm + b_nsp + b_pool);
+    char* hdr = b + 2 * b_plane + b_nrm + b_nsp + 2 * b_pool;
+    int* status = reinterpret_cast<int*>(hdr);
+    float* center = reinterpret_cast<float*>(hdr + 16);
+    PrepJob pj = make_prep_job(g, img, center, p0, p1, nrm, nsp);
+    pj.status = status;
+    cudaError_t e;
+    if ((e = launch_center_batch(&pj, 1, st)) != cudaSuccess || (e = launch_planes_batch(&pj, 1, st)) != cudaSuccess ||
+        (e = launch_box_batch(&pj, 1, st)) != cudaSuccess)
+        return set_error(BM_ERR_CUDA, (std::string("ncc preparation: ") + cudaGetErrorString(e)).c_str());
+    TcArgs a{};
+    a.plane0 = p0;
+    a.plane1 = p1;
+    a.nrm = nrm;
+    a.nsp = nsp;
+    a.pool_idx = pidx;
+    a.pool_score = pscore;
+    a.status = status;
+    a.fault = ctx_fault_word(ctx);
+    if ((e = launch_tc_batch(&g, &a, 1, st)) != cudaSuccess)
+        return set_error(BM_ERR_CUDA, (std::string("ncc tensor-core launch: ") + cudaGetErrorString(e)).c_str());
+    NccPoolParams Q{};
+    Q.img = img; Q.nrm = nrm; Q.pool_idx = pidx; Q.pool_score = pscore;
+    Q.out_idx = out_idx; Q.out_score = out_score; Q.counters = ctx_counters(ctx);
+    Q.H = g.H; Q.W = g.W; Q.C = g.C; Q.p = g.p; Q.h = g.h; Q.s = g.s; Q.K = g.K; Q.L = g.L;
+    Q.n_ry = g.n_ry; Q.n_rx = g.n_rx; Q.Hc = g.Hc; Q.Wc = g.Wc; Q.u8 = g.dtype == kU8;
+    Q.eps = 6.103515625e-05f;  // 2^-14: the split cross term's bound, as in block matching
+    const int tb = tc_score_bits(g);
+    Q.round_rel = tb ? ldexpf(1.0f, tb - 23) : 0.0f;
+    const unsigned blocks = (unsigned)((g.nR + 3) / 4);
+    if (Q.u8) ncc_pool_kernel<true><<<blocks, 128, 0, st>>>(Q);
+    else ncc_pool_kernel<false><<<blocks, 128, 0, st>>>(Q);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return set_error(BM_ERR_CUDA, (std::string("ncc pool launch: ") + cudaGetErrorString(e)).c_str());
+    ctx_count_tc_job(ctx);
+    return BM_OK;
+}
+
 }  // namespace
 }  // namespace bm
 
@@ -443,6 +698,21 @@ int bm_match_ncc(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dty
     if (patch * patch * C > kMaxPatchElems)
         return set_error(BM_ERR_UNSUPPORTED, "patch*patch*C must be at most 256");
     if (K > kNccMaxK) return set_error(BM_ERR_UNSUPPORTED, "K must be at most 64 for NCC");
+    DevGuard dg0(ctx_device(ctx));
+    if (dtype == BM_U8) {
+        // the tensor-core form (uint8, K <= 32, the class fits the kernel).
+        // float32 stays on the CUDA-core kernels: its tensor-core form needs
+        // the three-product split and a direct re-rank of the pool, and
+        // measured slower (687 against 378 us per 512 x 512 image)
+        Geom g;
+        if (make_geom(g, H, W, C, (int)dtype, patch, window, stride, K) == BM_OK) {
+            g.ncc = 1;
+            // a pool of 32 (one entry per lane) or K + 8: NCC scores cluster near the top
+            g.L = std::min(160, std::max(32, (K + 8 + 7) / 8 * 8));
+            if (K <= 32 && ctx_uses_tc(ctx) && tc_supported(g))
+                return ncc_tensor_core(ctx, g, img, out_idx, out_score, reinterpret_cast<cudaStream_t>(stream));
+        }
+    }
     NccParams Q{};
     Q.img = img; Q.out_idx = out_idx; Q.out_score = out_score;
     Q.H = H; Q.W = W; Q.C = C; Q.p = patch; Q.h = (window - 1) / 2; Q.s = stride; Q.K = K;

@@ -72,7 +72,7 @@ constexpr int kCenterThreads = 512;
 __global__ void __launch_bounds__(kCenterThreads) center_kernel(const __grid_constant__ PrepParams P) {
     const PrepJob& J = P.jobs[blockIdx.x];
     if (threadIdx.x == 0 && J.status) *J.status = 0;
-    if (J.dtype != kF32) {
+    if (J.dtype != kF32 || J.ncc) {
         if (threadIdx.x == 0) *J.center = 0.f;  // uint8: constant offset, nothing to compute
         return;
     }
@@ -127,7 +127,8 @@ template <bool kIsU8>
 __global__ void planes_kernel(const __grid_constant__ PrepParams P) {
     const PrepJob& J = P.jobs[blockIdx.y];
     if ((J.dtype == (int)DType::kU8) != kIsU8) return;
-    const float c0 = kIsU8 ? (float)kCenterU8 : *J.center;
+    const float c0 = J.ncc ? 0.f : kIsU8 ? (float)kCenterU8 : *J.center;
+    const bool two = !kIsU8 || J.ncc;  // a lo plane (zero for uint8: exact in bf16)
     const int vec_per_row = J.plane_pitch / 8;
     const size_t total = (size_t)J.plane_rows * vec_per_row;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
@@ -147,7 +148,7 @@ __global__ void planes_kernel(const __grid_constant__ PrepParams P) {
             }
             __nv_bfloat16 h = __float2bfloat16_rn(v);
             hi[i] = __bfloat16_as_ushort(h);
-            if (!kIsU8) lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+            lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
         }
         uint4 vh, vl;
         vh.x = hi[0] | (uint32_t(hi[1]) << 16);
@@ -155,7 +156,7 @@ __global__ void planes_kernel(const __grid_constant__ PrepParams P) {
         vh.z = hi[4] | (uint32_t(hi[5]) << 16);
         vh.w = hi[6] | (uint32_t(hi[7]) << 16);
         reinterpret_cast<uint4*>(J.plane0)[t] = vh;
-        if (!kIsU8) {
+        if (two) {
             vl.x = lo[0] | (uint32_t(lo[1]) << 16);
             vl.y = lo[2] | (uint32_t(lo[3]) << 16);
             vl.z = lo[4] | (uint32_t(lo[5]) << 16);
@@ -199,9 +200,10 @@ __global__ void __launch_bounds__(kBoxThreads) box_kernel(const __grid_constant_
         const size_t base = ((size_t)(y0 + r) * J.W + (x0 + c)) * C;
         if (kIsU8) {
             const uint8_t* row = static_cast<const uint8_t*>(J.img) + base;
+            const int cu = J.ncc ? 0 : kCenterU8;
             int rs = 0;
             for (int e = 0; e < pc; ++e) {
-                const int v = (int)__ldg(row + e) - kCenterU8;
+                const int v = (int)__ldg(row + e) - cu;
                 rs += v * v;
             }
             hs[idx] = make_float2(__int_as_float(rs), 0.f);
@@ -254,7 +256,9 @@ __global__ void __launch_bounds__(kBoxThreads) box_kernel(const __grid_constant_
             if (r >= orows || c >= ocols) continue;
             const float o = outs[r * kBoxX + c];
             const float v = kIsU8 ? (float)__float_as_int(o) : o;
-            nsp[(size_t)(x0 + c) * J.Hc + (y0 + r)] = split_norm(v, !kIsU8);
+            nsp[(size_t)(x0 + c) * J.Hc + (y0 + r)] =
+                J.ncc ? make_uint4(__float_as_uint(v > 0.f ? rsqrtf(v) : 0.f), 0u, 0u, 0u)
+                      : split_norm(v, !kIsU8);
         }
     }
 }
@@ -322,6 +326,7 @@ PrepJob make_prep_job(const Geom& g, const void* img, float* center, uint16_t* p
     j.img = img; j.center = center; j.plane0 = plane0; j.plane1 = plane1; j.nrm = nrm; j.nsp = nsp;
     j.H = g.H; j.W = g.W; j.C = g.C; j.Cp = g.Cp; j.p = g.p; j.Hc = g.Hc; j.Wc = g.Wc;
     j.plane_pitch = g.plane_pitch; j.plane_rows = g.plane_rows; j.dtype = g.dtype;
+    j.ncc = g.ncc;
     return j;
 }
 

@@ -86,6 +86,7 @@ struct TcGeom {
     int f32;
     int a_bytes;
     int ts, a_cols;           // A operand in tensor memory (TS MMAs): columns per slot (0: SS)
+    int ncc, off_g;           // NCC scores: per-warp 1 / ||X_j|| rows of a column (slot offset)
     int off_base, off_a, off_stage, off_buf, slot_bytes;  // inside a slot's region
     int off_slots, off_an, off_heap, off_bar, smem_total;
 };
@@ -1014,7 +1015,8 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                             while (qq >= G.pw) { qq -= G.pw; ++u; }
                         }
                     }
-                    mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
+                    if (!G.ncc)  // NCC: no norm K-step (the score is scaled in the epilogue)
+                        mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
                     mma_commit(BAR(k, kBarSEmpty + stage));
                     mma_commit(BAR(k, kBarTFull + buf));
                     if (c + 1 == T.c1) mma_commit(BAR(k, kBarAEmpty));  // A free once these finish
@@ -1103,9 +1105,30 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     const int b0 = wlo >> 4, nblk = (whi >> 4) - b0 + 1;
                     const uint32_t colbase = tmem_base + lane_base + (2 * k + buf) * G.bufcols +
                                              jl * G.Rb + 16 * b0;
+                    // NCC: 1 / ||X_j|| of this column's candidate rows, into the warp's
+                    // own shared-memory row (read back by broadcast)
+                    float* gw = reinterpret_cast<float*>(slot + G.off_g) + quarter * 256;
+                    if (G.ncc) {
+                        const uint4* gsrc = reinterpret_cast<const uint4*>(J.nsp) + (size_t)xc * J.Hc + T.Y0;
+                        for (int rr = 16 * b0 + lane; rr < 16 * (b0 + nblk); rr += 32)
+                            gw[rr] = T.Y0 + rr < J.Hc ? __uint_as_float(__ldg(&gsrc[rr].x)) : 0.f;
+                        __syncwarp();
+                    }
                     for (int bb = 0; bb < nblk; ++bb) {
                         float w[16], wmax;
                         tmem_ld_max(colbase + 16 * bb, w, wmax);
+                        if (G.ncc) {
+                            // the score a_j / ||X_j||: the maximum is of the scaled values
+                            const float4* g4 = reinterpret_cast<const float4*>(gw + 16 * (b0 + bb));
+                            wmax = -__int_as_float(0x7f800000);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 gq = g4[q];
+                                w[4 * q] *= gq.x; w[4 * q + 1] *= gq.y; w[4 * q + 2] *= gq.z; w[4 * q + 3] *= gq.w;
+                            }
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) wmax = fmaxf(wmax, w[i]);
+                        }
                         // a block whose values all fall below every lane's threshold
                         // adds nothing: skipped on the load's own maximum (which also
                         // covers rows outside a lane's window -- a false positive
@@ -1252,13 +1275,16 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     t = TcGeom{};
     t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
     t.pw = g.pw; t.p_eff = g.p_eff; t.nkc = g.p_eff * g.pw;
-    t.f32 = g.dtype == kF32;
+    // NCC keeps a pool by score for both dtypes (the float32 form of the
+    // kernel; uint8 operands are exact in its hi plane, its lo plane is 0)
+    t.ncc = g.ncc;
+    t.f32 = g.dtype == kF32 || g.ncc;
     t.HL = t.f32 ? g.L : g.K;
     const int nplanes = t.f32 ? 2 : 1;
     // float32 lists in registers use 32-bit keys when the window index fits
     // 12 bits (window <= 63): 2^-11 relative rounding of the pool scores
     t.tbits = 0;
-    if (t.f32 && t.HL <= 32) {
+    if (t.f32 && t.HL <= 32 && !t.ncc) {  // NCC: exact scores (its scores cluster near the top)
         const int ww = 2 * g.h + 1;
         int b = 1;
         while ((1 << b) < ww * ww) ++b;
@@ -1313,6 +1339,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
                     c.off_a = off; off += nplanes * c.a_bytes;
                     c.off_stage = off; off += nst * c.stage_bytes;
                     c.off_buf = off; off += 128 * kbuf * (c.tbits ? 4 : 8);  // 32- or 64-bit keys
+                    c.off_g = off; off += g.ncc ? 4 * 256 * 4 : 0;  // NCC: a column's 1/||X_j||, per warp
                     c.slot_bytes = (off + 1023) / 1024 * 1024;
                     off = 0;
                     c.off_slots = off; off += ns * c.slot_bytes;
@@ -1538,7 +1565,7 @@ int tc_score_bits(const Geom& g) {
 // Jobs that can share one persistent launch (same class geometry).
 bool tc_same_class(const Geom& a, const Geom& b) {
     return a.dtype == b.dtype && a.Cp == b.Cp && a.p == b.p && a.h == b.h && a.s == b.s &&
-           a.K == b.K && a.L == b.L;
+           a.K == b.K && a.L == b.L && a.ncc == b.ncc;
 }
 
 cudaError_t launch_tc(const Geom& g, const TcArgs& a, cudaStream_t st) {

@@ -123,3 +123,26 @@ def test_invalid_and_unsupported(ctx):
     assert rc == B.BM_ERR_INVALID
     torch.cuda.synchronize()
     assert bool((idx == -7).all()) and bool((sc == -7.0).all())
+
+
+@pytest.mark.parametrize("dt", ["u8"])
+def test_tensor_core_form_is_used_and_agrees(dt):
+    """bm_match_ncc runs its tensor-core form for a supported uint8 class
+    (the tensor-core job counter moves) and agrees exactly with the
+    CUDA-core kernels (BM_ALGO_DIRECT) and with the oracle."""
+    img = make_image(130, 121, 1, dt, seed=77)
+    tc = B.Context(0)
+    cc = B.Context(0)
+    cc.set_algo(B.BM_ALGO_DIRECT)
+    t = torch.from_numpy(img).cuda()
+    before = tc.stats()["tc_jobs"]
+    a_idx, a_sc = tc.match_ncc(t, 8, 39, 3, 16)
+    torch.cuda.synchronize()
+    assert tc.stats()["tc_jobs"] == before + 1
+    b_idx, b_sc = cc.match_ncc(t, 8, 39, 3, 16)
+    torch.cuda.synchronize()
+    assert cc.stats()["tc_jobs"] == 0
+    assert torch.equal(a_idx, b_idx) and torch.equal(a_sc, b_sc)
+    check(tc, img, 8, 39, 3, 16)
+    for c in (tc, cc):
+        c.close()
