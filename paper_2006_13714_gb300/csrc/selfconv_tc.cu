@@ -1015,7 +1015,8 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                             while (qq >= G.pw) { qq -= G.pw; ++u; }
                         }
                     }
-                    if (!G.ncc)  // NCC: no norm K-step (the score is scaled in the epilogue)
+                    // NCC (never 32-bit keys): no norm K-step (the score is scaled in the epilogue)
+                    if (K32 || !G.ncc)
                         mma_bf16(d, dn_a, sdesc(sbu + nplanes * G.plane_stage, 16, 128), idesc, 1);
                     mma_commit(BAR(k, kBarSEmpty + stage));
                     mma_commit(BAR(k, kBarTFull + buf));
@@ -1108,7 +1109,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     // NCC: 1 / ||X_j|| of this column's candidate rows, into the warp's
                     // own shared-memory row (read back by broadcast)
                     float* gw = reinterpret_cast<float*>(slot + G.off_g) + quarter * 256;
-                    if (G.ncc) {
+                    if (!K32 && G.ncc) {
                         const uint4* gsrc = reinterpret_cast<const uint4*>(J.nsp) + (size_t)xc * J.Hc + T.Y0;
                         for (int rr = 16 * b0 + lane; rr < 16 * (b0 + nblk); rr += 32)
                             gw[rr] = T.Y0 + rr < J.Hc ? __uint_as_float(__ldg(&gsrc[rr].x)) : 0.f;
@@ -1117,7 +1118,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     for (int bb = 0; bb < nblk; ++bb) {
                         float w[16], wmax;
                         tmem_ld_max(colbase + 16 * bb, w, wmax);
-                        if (G.ncc) {
+                        if (!K32 && G.ncc) {
                             // the score a_j / ||X_j||: the maximum is of the scaled values
                             const float4* g4 = reinterpret_cast<const float4*>(gw + 16 * (b0 + bb));
                             wmax = -__int_as_float(0x7f800000);
