@@ -424,6 +424,43 @@ struct Heap {
     }
 };
 
+// The same heap with 32-bit keys (float32 pools over 32 entries whose
+// window index fits the key's low bits): half the shared memory and traffic.
+struct Heap32 {
+    unsigned* h;
+    int n;
+    __device__ __forceinline__ unsigned top() const { return h[0]; }
+    __device__ void replace_top(unsigned key) {
+        int i = 0;
+        while (true) {
+            const int c0 = 4 * i + 1;
+            if (c0 >= n) break;
+            unsigned cv = h[c0 * 128];
+            int c = c0;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                const int ck = c0 + k;
+                const unsigned v = ck < n ? h[ck * 128] : 0u;
+                if (v > cv) { cv = v; c = ck; }
+            }
+            if (cv <= key) break;
+            h[i * 128] = cv;
+            i = c;
+        }
+        h[i * 128] = key;
+    }
+    __device__ void sort() {
+        const int n0 = n;
+        for (int m = n0 - 1; m > 0; --m) {
+            const unsigned mx = h[0], last = h[m * 128];
+            h[m * 128] = mx;
+            n = m;
+            replace_top(last);
+        }
+        n = n0;
+    }
+};
+
 // Compare-exchange: x <- min, y <- max.
 __device__ __forceinline__ void cmpx(unsigned long long& x, unsigned long long& y) {
     const bool s = y < x;
@@ -561,6 +598,19 @@ __device__ __noinline__ RegTopK<LC, unsigned> final_merge32(unsigned* pend, int 
     float thr = 0.f;
     merge_pending32(pend, cnt, thr, reg, M);
     return reg;
+}
+
+// 32-bit pending keys into the lane's shared-memory heap (pools over 32).
+__device__ __forceinline__ void merge_pending32_heap(unsigned* pend, int& cnt, float& thr, Heap32& heap,
+                                                     unsigned M) {
+    for (int j = 0; j < cnt; ++j) {
+        const unsigned key = pend[j * 128];
+        if (key < heap.top()) heap.replace_top(key);
+    }
+    cnt = 0;
+    const unsigned t = heap.top();
+    // lowest value whose key can still beat the heap's worst entry
+    if (t != ~0u) thr = from_orderable(~(t | M));
 }
 
 // Warp-synchronous merge of every lane's pending entries (call from all 32
@@ -1043,6 +1093,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
         const unsigned kM = (1u << G.tbits) - 1u;   // window-index bits of a 32-bit key
         const int ww = 2 * G.h + 1;
         Heap heap{reinterpret_cast<unsigned long long*>(smem + G.off_heap) + (threadIdx.x & 127), G.HL};
+        Heap32 heap32{reinterpret_cast<unsigned*>(smem + G.off_heap) + (threadIdx.x & 127), G.HL};
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         int qc = 0;  // slot-local chunk counter (accumulator phase)
         for (int turn = 0; !*abort_flag; ++turn) {
@@ -1051,10 +1102,12 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             const TileInfo T = tile_info(P, tile);
             const TcJob& J = *T.job;
             RegTopK<LC == 0 ? 1 : LC> reg;
-            RegTopK<K32 ? LC : 32, unsigned> reg32;
-            if constexpr (K32) reg32.init(G.HL);
-            else reg.init(G.HL);
-            if constexpr (LC == 0) {
+            RegTopK<(K32 && LC > 0) ? LC : 32, unsigned> reg32;
+            if constexpr (K32 && LC > 0) reg32.init(G.HL);
+            else if constexpr (LC > 0) reg.init(G.HL);
+            if constexpr (LC == 0 && K32) {
+                for (int i = 0; i < G.HL; ++i) heap32.h[i * 128] = ~0u;
+            } else if constexpr (LC == 0) {
                 for (int i = 0; i < G.HL; ++i) heap.h[i * 128] = kEmpty;
             }
             const int ry = T.ry0 + (quarter / G.wgx) * G.rr + lane / G.rc;
@@ -1192,7 +1245,8 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                         }
                         // keep room for the next block's appends
                         if (__any_sync(0xffffffffu, cnt >= merge_at)) {
-                            if constexpr (K32) merge_pending32(pend32, cnt, thr, reg32, kM);
+                            if constexpr (K32 && LC == 0) merge_pending32_heap(pend32, cnt, thr, heap32, kM);
+                            else if constexpr (K32) merge_pending32(pend32, cnt, thr, reg32, kM);
                             else merge_pending<LC, kF32, 128>(G, nrm_i, nr_i, pend, cnt, thr, reg, heap);
                         }
                     }
@@ -1201,14 +1255,18 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 mbar_arrive(BAR(k, kBarTEmpty + buf));
             }
             if (__any_sync(0xffffffffu, cnt > 0)) {
-                if constexpr (K32) reg32 = final_merge32(pend32, cnt, reg32, kM);
+                if constexpr (K32 && LC == 0) {
+                    float thr0 = 0.f;
+                    merge_pending32_heap(pend32, cnt, thr0, heap32, kM);
+                } else if constexpr (K32) reg32 = final_merge32(pend32, cnt, reg32, kM);
                 else reg = final_merge<LC, kF32, 128>(G, nrm_i, nr_i, pend, cnt, reg, heap.h);
             }
             // ---- write results
             if (lane_ok && !*abort_flag) {
                 // a window part writes its own list (merged by split_merge_kernel)
                 const size_t ref = (size_t)ry * J.n_rx + rx + (size_t)T.part * J.n_ry * J.n_rx;
-                if constexpr (LC == 0) heap.sort();  // outputs and pools best first
+                if constexpr (LC == 0 && K32) heap32.sort();  // outputs and pools best first
+                else if constexpr (LC == 0) heap.sort();
                 const int nout = kF32 ? G.HL : G.K;
                 auto emit = [&](int i, unsigned long long key) {
                     if (kF32) {
@@ -1226,21 +1284,24 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     }
                 };
                 if constexpr (K32) {
-#pragma unroll
-                    for (int i = 0; i < LC; ++i) {
-                        if (i < nout) {
-                            const unsigned key = reg32.a[i];
-                            int32_t off = -1;
-                            float v = -__int_as_float(0x7f800000);
-                            if (key != ~0u) {
-                                const int li = (int)(key & kM);
-                                const int dy = li / ww - G.h, dx = li % ww - G.h;
-                                off = (yr + dy) * J.W + (xr + dx);
-                                v = from_orderable(~(key & ~kM));  // upper end of the key's bucket
-                            }
-                            J.pool_idx[ref * G.HL + i] = off;
-                            J.pool_score[ref * G.HL + i] = v;
+                    auto emit32 = [&](int i, unsigned key) {
+                        int32_t off = -1;
+                        float v = -__int_as_float(0x7f800000);
+                        if (key != ~0u) {
+                            const int li = (int)(key & kM);
+                            const int dy = li / ww - G.h, dx = li % ww - G.h;
+                            off = (yr + dy) * J.W + (xr + dx);
+                            v = from_orderable(~(key & ~kM));  // upper end of the key's bucket
                         }
+                        J.pool_idx[ref * G.HL + i] = off;
+                        J.pool_score[ref * G.HL + i] = v;
+                    };
+                    if constexpr (LC > 0) {
+#pragma unroll
+                        for (int i = 0; i < LC; ++i)
+                            if (i < nout) emit32(i, reg32.a[i]);
+                    } else {
+                        for (int i = 0; i < nout; ++i) emit32(i, heap32.h[i * 128]);
                     }
                 } else if constexpr (LC > 0) {
 #pragma unroll
@@ -1283,13 +1344,25 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     t.HL = t.f32 ? g.L : g.K;
     const int nplanes = t.f32 ? 2 : 1;
     // float32 lists in registers use 32-bit keys when the window index fits
-    // 12 bits (window <= 63): 2^-11 relative rounding of the pool scores
-    t.tbits = 0;
-    if (t.f32 && t.HL <= 32 && !t.ncc) {  // NCC: exact scores (its scores cluster near the top)
+    // 12 bits (window <= 63): up to 2^-11 relative rounding of the pool
+    // scores.  Pools over 32 (the shared-memory heap) keep 64-bit keys when
+    // they fit -- the rounding widens the re-rank's band, which for K 70 at
+    // window 61 sent a quarter of the references to a window recompute --
+    // and take 32-bit keys (half the heap) only when nothing else fits.
+    int tb32 = 0;
+    if (t.f32 && !t.ncc) {  // NCC: exact scores (its scores cluster near the top)
         const int ww = 2 * g.h + 1;
         int b = 1;
         while ((1 << b) < ww * ww) ++b;
-        if (b <= 12) t.tbits = b;
+        if (b <= 12) tb32 = b;
+    }
+    t.tbits = t.HL <= 32 ? tb32 : 0;
+    const TcGeom t0 = t;
+    for (int keys = 0; keys < 2; ++keys) {
+    if (keys == 1) {
+        if (t.HL <= 32 || !tb32) break;
+        t = t0;
+        t.tbits = tb32;
     }
     // lane -> reference mapping: rr reference rows x rc columns per warp, a
     // wgy x wgx grid of 4 warps
@@ -1345,7 +1418,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
                     off = 0;
                     c.off_slots = off; off += ns * c.slot_bytes;
                     c.off_an = off; off += 128 * 2 * 16;
-                    c.off_heap = off; off += c.HL > 32 ? 128 * c.HL * 8 : 0;
+                    c.off_heap = off; off += c.HL > 32 ? 128 * c.HL * (c.tbits ? 4 : 8) : 0;
                     c.off_bar = off; off += ns * kBarsPerSlot * 8 + 16;
                     c.smem_total = (off + 1023) / 1024 * 1024;
                     if (c.smem_total > kSmemLimit) continue;
@@ -1371,6 +1444,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
             return true;
         }
     }
+    }  // keys
     return false;
 }
 
@@ -1527,7 +1601,7 @@ cudaError_t launch_params(TcParams& P, cudaStream_t st) {
         else kern = T.HL <= 16 ? tc_match_kernel<16, false, 2, false> : tc_match_kernel<32, false, 2, false>;
     } else {
         threads = cta_threads(1);
-        if (T.f32) kern = T.HL > 32 ? tc_match_kernel<0, true, 1, false>
+        if (T.f32) kern = T.HL > 32 ? (T.tbits ? tc_match_kernel<0, true, 1, true> : tc_match_kernel<0, true, 1, false>)
                         : !T.tbits ? tc_match_kernel<32, true, 1, false>
                         : T.HL <= 24 ? tc_match_kernel<24, true, 1, true> : tc_match_kernel<32, true, 1, true>;
         else kern = T.HL <= 16 ? tc_match_kernel<16, false, 1, false>
