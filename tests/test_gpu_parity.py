@@ -232,6 +232,7 @@ TS_CASES = [
     ("ts_u8_c4_p8_k70", 110, 97, 4, "u8", 8, 61, 3, 70),
     ("ts_u8_c4_p7_k70", 90, 99, 4, "u8", 7, 39, 4, 70),
     ("ts_f32_c4_p8_w61", 100, 96, 4, "f32", 8, 61, 3, 16),
+    ("ts_f32_c4_k70_heap32", 104, 99, 4, "f32", 8, 39, 3, 70),   # 32-bit-key heap
 ]
 
 
