@@ -484,13 +484,12 @@ int branch_streams(bm_ctx* ctx, cudaStream_t st, int n, std::vector<cudaStream_t
 // zeroes the words).
 int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, void* ws,
                   const size_t* offs, cudaStream_t st, bool count, int* job_status = nullptr) {
-    std::vector<int> tc_ids;
+    std::vector<int> tc_ids, direct_ids;
     std::vector<TcArgs> args(n);
     std::vector<PrepJob> pjs;
     for (int i = 0; i < n; ++i) {
         if (!use_tc(ctx, gs[i])) {
-            int rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, st);
-            if (rc != BM_OK) return rc;
+            direct_ids.push_back(i);
         } else {
             PrepJob pj;
             job_views(gs[i], reqs[i], static_cast<char*>(ws) + offs[i], pj, args[i]);
@@ -500,6 +499,22 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
             tc_ids.push_back(i);
         }
     }
+    // direct-kernel jobs beside tensor-core jobs run on a branch of their own,
+    // forked here (they depend on nothing of this batch) and joined at the end,
+    // so they overlap the tensor-core work instead of preceding it
+    cudaEvent_t ev_dfork = nullptr;
+    const bool fork_direct = !direct_ids.empty() && !tc_ids.empty() && !ctx->timing.load();
+    if (fork_direct) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev_dfork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_dfork, st);
+        if (e != cudaSuccess) return cuda_fail(e, "direct fork");
+    } else {
+        for (int i : direct_ids) {
+            int rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, st);
+            if (rc != BM_OK) return rc;
+        }
+    }
+    int nbranch = 0;  // class branches the tensor-core part used
     if (!tc_ids.empty()) {
         int rc = prep_jobs(ctx, pjs.data(), (int)pjs.size(), st);
         if (rc != BM_OK) return rc;
@@ -539,6 +554,7 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
         if (fork) {
             int rc = branch_streams(ctx, st, ncls - 1, br);
             if (rc != BM_OK) return rc;
+            nbranch = ncls - 1;
         }
         cudaEvent_t ev_fork = nullptr;
         std::vector<cudaEvent_t> ev_join;
@@ -588,6 +604,24 @@ int enqueue_batch(bm_ctx* ctx, const Geom* gs, const bm_request* reqs, int n, vo
         }
         if (ev_fork) cudaEventDestroy(ev_fork);
         for (cudaEvent_t ej : ev_join) cudaEventDestroy(ej);
+    }
+    if (fork_direct) {
+        std::vector<cudaStream_t> br;
+        int rc = branch_streams(ctx, st, nbranch + 1, br);
+        if (rc != BM_OK) return rc;
+        cudaStream_t sd = br.back();
+        cudaError_t e = cudaStreamWaitEvent(sd, ev_dfork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "direct fork");
+        for (int i : direct_ids) {
+            rc = enqueue_job(ctx, gs[i], reqs[i], nullptr, sd);
+            if (rc != BM_OK) return rc;
+        }
+        cudaEvent_t ej = nullptr;
+        if ((e = cudaEventCreateWithFlags(&ej, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventRecord(ej, sd)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ej, 0)) != cudaSuccess)
+            return cuda_fail(e, "direct join");
+        cudaEventDestroy(ej);
+        cudaEventDestroy(ev_dfork);
     }
     if (count) {
         for (int i = 0; i < n; ++i) {

@@ -168,14 +168,15 @@ def test_autotuner_picks_a_configuration_with_identical_results(tmp_path, dt):
 
 
 def test_mixed_class_batch_graph_replay():
-    """Several classes in one bm_match_batch: their launches run on parallel
-    branches of one captured graph.  Replays with new pixels give what each
-    job gives alone."""
+    """Several classes in one bm_match_batch (one of them on the direct
+    kernel): their launches run on parallel branches of one captured graph.
+    Replays with new pixels give what each job gives alone."""
     ctx = B.Context(0)
     st = torch.cuda.Stream()
     specs = [(100, 90, 1, "f32", 8, 39, 3, 16), (64, 64, 1, "u8", 8, 21, 1, 16),
              (80, 72, 4, "u8", 8, 39, 3, 32), (150, 133, 1, "f32", 7, 61, 4, 70),
-             (96, 96, 1, "u8", 7, 39, 4, 32)]
+             (96, 96, 1, "u8", 7, 39, 4, 32),
+             (90, 84, 4, "f32", 8, 61, 3, 32)]  # a direct-kernel class: its own branch
     imgs, outs, reqs = [], [], []
     for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
         t = torch.from_numpy(_image(H, W, C, dt, 300 + i)).cuda()
