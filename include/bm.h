@@ -420,8 +420,12 @@ size_t bm_workspace_bytes(int H, int W, int C, bm_dtype dtype, int patch, int wi
  * separate CTAs run; each part keeps its own top-K list (float32: pool),
  * and a merge kernel combines them, so results are identical to an unsplit
  * run.  A launch with enough tiles (a batch of many images) does not split.
- * Returns 1 (no split), 2 or 4; 0 for invalid arguments.  bm_match_static
- * never splits.
+ * Classes whose staged tile does not fit shared memory whole (float32 four-
+ * channel at window 61 with K above 16 or patch 7; large windows) always
+ * run split into 2, 3 or 4 contiguous column parts, each staging only its
+ * own columns, in every entry point, bm_match_static included.  Returns 1
+ * (no split), 2, 3 or 4; 0 for invalid arguments.  Apart from those
+ * classes, bm_match_static never splits.
  */
 int bm_window_split(int H, int W, int C, bm_dtype dtype, int patch, int window, int stride, int K);
 

@@ -195,6 +195,9 @@ bool tc_same_class(const Geom& a, const Geom& b);
 // Parts per tile the window split may use for a job (1: never split);
 // TcArgs.wsplit and the part-list room follow it.
 int tc_window_split(const Geom& g);
+// Column parts of the job's class (1: none).  Above 1 the job always runs
+// split in that many parts and needs the part-list room.
+int tc_column_parts(const Geom& g);
 
 // (a6) float32 boundary re-rank: direct recomputation of the pool's band,
 // FP64 only for ties at the K-th boundary; writes the final outputs.

@@ -48,7 +48,8 @@ size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 // offset 16) and the re-rank counters (4 x u64, offset 32); the header is the
 // only part that must start at zero, and each call clears it.
 struct Layout {
-    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, total;
+    size_t plane0, plane1, nrm, nsp, pool_idx, pool_score, split, total;
+    int parts;  // column parts of the class (their part lists follow the pool)
 };
 constexpr size_t kHeader = 256;
 constexpr size_t kCenterOff = 16;
@@ -64,6 +65,9 @@ Layout layout(const Geom& g) {
         l.nsp = off; off += round256(nsp_bytes(g));
         l.pool_idx = off; off += g.dtype == kF32 ? round256((size_t)g.nR * g.L * 4) : 0;
         l.pool_score = off; off += g.dtype == kF32 ? round256((size_t)g.nR * g.L * 4) : 0;
+        l.parts = tc_column_parts(g);
+        const size_t nlist = (size_t)g.nR * (g.dtype == kF32 ? g.L : g.K);
+        l.split = off; off += l.parts > 1 ? 2 * round256((size_t)l.parts * nlist * 4) : 0;
     }
     l.total = off;
     return l;
@@ -180,6 +184,12 @@ extern "C" int bm_match_static(const void* img, int H, int W, int C, bm_dtype dt
     } else {
         a.pool_idx = reinterpret_cast<int32_t*>(b + l.pool_idx);
         a.pool_score = reinterpret_cast<float*>(b + l.pool_score);
+    }
+    if (l.parts > 1) {  // column parts: the parts' lists, merged by the launch
+        const size_t nlist = (size_t)g.nR * (g.dtype == kF32 ? g.L : g.K);
+        a.wsplit = l.parts;
+        a.split_idx = reinterpret_cast<int32_t*>(b + l.split);
+        a.split_val = reinterpret_cast<int32_t*>(b + l.split + round256((size_t)l.parts * nlist * 4));
     }
     if ((e = launch_tc(g, a, st)) != cudaSuccess) return launch_fail(e, "tensor-core kernel launch");
     if (g.dtype == kF32) {

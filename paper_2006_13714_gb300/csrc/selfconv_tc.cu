@@ -87,6 +87,8 @@ struct TcGeom {
     int a_bytes;
     int ts, a_cols;           // A operand in tensor memory (TS MMAs): columns per slot (0: SS)
     int ncc, off_g;           // NCC scores: per-warp 1 / ||X_j|| rows of a column (slot offset)
+    int xs;                   // column parts: each part of a tile's candidate columns stages
+                              //   only its own columns (1: the whole union in one tile)
     int off_base, off_a, off_stage, off_buf, slot_bytes;  // inside a slot's region
     int off_slots, off_an, off_heap, off_bar, smem_total;
 };
@@ -94,6 +96,8 @@ struct TcGeom {
 // One image of a launch.
 struct TcJob {
     CUtensorMap map[2];       // bf16 planes (hi / exact, lo) as {8 elements, row chunks, rows}
+    const uint16_t* plane[2]; // the same planes (A read from global memory with column parts)
+    int pitch;                // plane row pitch (elements)
     const uint16_t* nsp;      // split norms [Wc][Hc][8] bf16
     const void* nrm;          // int32 / float32 norms [Hc][Wc]
     int32_t* out_idx;         // uint8: final indices
@@ -312,13 +316,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         : "memory");
 }
 
-// 16 bytes of a staged row starting at element e (any alignment; per-lane e).
-__device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
-    const uint4* s = reinterpret_cast<const uint4*>(row + (e >> 3) * 16);
-    const uint4 A = s[0];
-    const int sh = e & 7;
-    if (sh == 0) return A;
-    const uint4 B = s[1];
+// The 16 bytes starting sh bf16 elements into the 32 bytes {A, B}.
+__device__ __forceinline__ uint4 shifted16(const uint4& A, const uint4& B, int sh) {
     const uint32_t w[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
     const int j = sh >> 1;
     uint32_t v[5];
@@ -328,6 +327,20 @@ __device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
     const uint32_t f = (sh & 1) * 16;
     return make_uint4(__funnelshift_r(v[0], v[1], f), __funnelshift_r(v[1], v[2], f),
                       __funnelshift_r(v[2], v[3], f), __funnelshift_r(v[3], v[4], f));
+}
+// 16 bytes of a staged row starting at element e (any alignment; per-lane e).
+__device__ __forceinline__ uint4 lds_shifted16(const uint8_t* row, int e) {
+    const uint4* s = reinterpret_cast<const uint4*>(row + (e >> 3) * 16);
+    const int sh = e & 7;
+    return sh == 0 ? s[0] : shifted16(s[0], s[1], sh);
+}
+// The same from a plane row in global memory (16-byte aligned rows; the
+// plane pitch leaves room for the second chunk).
+__device__ __forceinline__ uint4 ldg_shifted16(const uint16_t* row, int e) {
+    const uint4* s = reinterpret_cast<const uint4*>(row + (e & ~7));
+    const int sh = e & 7;
+    const uint4 A = __ldg(s);
+    return sh == 0 ? A : shifted16(A, __ldg(s + 1), sh);
 }
 
 // Words J .. J+3 of the 32 bytes {a, b}, each shifted right by f bits
@@ -692,6 +705,9 @@ struct TileInfo {
     int ry0, rx0, ry_last, rx_last;
     int Y0, X0, NR, NX, nchunks, center_chunk;
     int part, c0, c1;  // window split: this part's chunks [c0, c1) of the visiting order
+                       // (column parts: positional chunks [c0, c1))
+    int xs0, pc;       // column parts: first staged candidate column (from X0), and the
+                       // chunk the part visits first (relative to c0); 0 otherwise
 };
 
 // Work item t of the launch: its job (binary search over the jobs' first
@@ -727,7 +743,21 @@ __device__ __forceinline__ TileInfo tile_info(const TcParams& P, int t) {
     T.center_chunk = min(T.nchunks - 1, ((T.rx0 + T.rx_last) * G.s / 2 - T.X0) / G.kcols);
     T.c0 = T.part * T.nchunks / J.wsplit;
     T.c1 = (T.part + 1) * T.nchunks / J.wsplit;
+    T.xs0 = 0;
+    T.pc = 0;
+    if (G.xs > 1) {
+        // column parts: contiguous chunks, visited from the one nearest the
+        // tile's centre outwards; the part's staged tile starts at its first
+        T.xs0 = T.c0 * G.kcols;
+        T.pc = max(0, min(T.center_chunk, T.c1 - 1) - T.c0);
+    }
     return T;
+}
+
+// Chunk (in column order) of the c-th step of a tile's visiting order.
+__device__ __forceinline__ int chunk_at(const TcGeom& G, const TileInfo& T, int c) {
+    return G.xs > 1 ? T.c0 + chunk_order(c - T.c0, T.c1 - T.c0, T.pc)
+                    : chunk_order(c, T.nchunks, T.center_chunk);
 }
 
 // Tile of slot k's g-th turn in CTA b (static round robin over the launch).
@@ -803,7 +833,9 @@ __device__ __forceinline__ void form_A(const TcGeom& G, const TileInfo& T, const
 // does not fit in shared memory beside the staged tile): each epilogue lane
 // writes its own row (TMEM lane m = A row m = reference m of the tile), the
 // K elements two per 32-bit column -- 16-byte chunk kc of plane pl at
-// columns a_row + (pl * nkc + kc) * 4.  The same values as form_A.
+// columns a_row + (pl * nkc + kc) * 4.  The same values as form_A.  With
+// column parts the staged tile need not hold the references' columns, and
+// the rows come from the planes in global memory instead.
 template <bool kF32>
 __device__ __forceinline__ void form_A_tmem(const TcGeom& G, const TileInfo& T, const TcJob& J,
                                             const uint8_t* sbase, int delta, uint32_t a_row, int m) {
@@ -817,8 +849,13 @@ __device__ __forceinline__ void form_A_tmem(const TcGeom& G, const TileInfo& T, 
             const int u = kc / G.pw, q = kc - u * G.pw;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (ok && u < G.p) {
-                const uint8_t* row = sbase + pl * G.base_bytes + (ry * G.s - T.Y0 + u) * G.base_pitch;
-                v = lds_shifted16(row, delta + (rx * G.s - T.X0) * G.Cp + 8 * q);
+                if (G.xs > 1) {
+                    v = ldg_shifted16(J.plane[pl] + (size_t)(ry * G.s + u) * J.pitch,
+                                      rx * G.s * G.Cp + 8 * q);
+                } else {
+                    const uint8_t* row = sbase + pl * G.base_bytes + (ry * G.s - T.Y0 + u) * G.base_pitch;
+                    v = lds_shifted16(row, delta + (rx * G.s - T.X0) * G.Cp + 8 * q);
+                }
                 const int valid = G.p * G.Cp - 8 * q;
                 uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -921,7 +958,9 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
             if (tile >= P.total_tiles) break;
             const TileInfo T = tile_info(P, tile);
             const TcJob& J = *T.job;
-            const int e0 = (T.X0 * G.Cp) & ~7, delta = T.X0 * G.Cp - e0;
+            // (column parts: the staged tile starts at the part's first column)
+            const int xst = (T.X0 + T.xs0) * G.Cp;
+            const int e0 = xst & ~7, delta = xst - e0;
             // (1) stage the tile plus halo: this warp is done reading the
             // previous one, and the epilogue warps are once the previous A is formed
             if (turn > 0 && !__all_sync(0xffffffffu, mbar_wait(BAR(k, kBarAFull), (turn - 1) & 1, abort_flag, 7)))
@@ -956,7 +995,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                     break;
                 }
                 uint8_t* sb = slot + G.off_stage + stage * G.stage_bytes;
-                const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                const int jc0 = chunk_at(G, T, c) * G.kcols;
                 const int kc_here = min(G.kcols, T.NX - jc0);
                 if (lane == 0) {
                     uint8_t* nsb = sb + nplanes * G.plane_stage;
@@ -968,7 +1007,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 }
                 for (int q = 0; q < G.pw; ++q)
                     for (int jl = 0; jl < kc_here; ++jl) {
-                        const int ecol = delta + (jc0 + jl) * G.Cp + 8 * q;
+                        const int ecol = delta + (jc0 - T.xs0 + jl) * G.Cp + 8 * q;
                         const uint8_t* const src[2] = {sbase + (ecol >> 3) * 16,
                                                        sbase + G.base_bytes + (ecol >> 3) * 16};
                         uint8_t* const dst[2] = {sb + q * G.qpitch + jl * G.Rb * 16,
@@ -1015,6 +1054,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 if (tile >= P.total_tiles) break;
                 const TileInfo T = tile_info(P, tile);
                 if (!mbar_wait(BAR(k, kBarAFull), turn & 1, abort_flag, 7)) break;
+                if (T.c0 == T.c1) mma_commit(BAR(k, kBarAEmpty));  // a part with no columns
                 for (int c = T.c0; c < T.c1; ++c, ++cs) {
                     const int stage = cs % G.nst, use = cs / G.nst;
                     const int buf = cs & 1, ub = cs >> 1;
@@ -1027,7 +1067,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                         break;
                     }
                     tc_fence_after();
-                    const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                    const int jc0 = chunk_at(G, T, c) * G.kcols;
                     const int kc_here = min(G.kcols, T.NX - jc0);
                     const uint32_t idesc = idesc_bf16(128, kc_here * G.Rb);
                     const uint32_t d = tmem_base + (2 * k + buf) * G.bufcols;
@@ -1147,7 +1187,7 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
                 const int buf = qc & 1, ub = qc >> 1;
                 if (!mbar_wait(BAR(k, kBarTFull + buf), ub & 1, abort_flag, 4)) break;
                 tc_fence_after();
-                const int jc0 = chunk_order(c, T.nchunks, T.center_chunk) * G.kcols;
+                const int jc0 = chunk_at(G, T, c) * G.kcols;
                 const int kc_here = min(G.kcols, T.NX - jc0);
                 for (int jl = 0; jl < kc_here; ++jl) {
                     const int xc = T.X0 + jc0 + jl;
@@ -1332,7 +1372,11 @@ tc_match_kernel(const __grid_constant__ TcParams P) {
 // Class geometry for a job shape: lane mapping, strips, slots, shared memory.
 // Preference: two tiles in flight (when the list lives in registers), then
 // the mapping with the least MMA work, then the largest append buffer and
-// the deepest stage ring that fit the shared memory.
+// the deepest stage ring that fit the shared memory.  Classes where nothing
+// fits split each tile's candidate columns into xs = 2, 3 or 4 contiguous
+// parts (separate work items whose lists the split merge joins), each
+// staging only its own columns: the staged tile shrinks by about xs, and A
+// (in tensor memory) is read from the planes in global memory.
 bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nullptr) {
     t = TcGeom{};
     t.Cp = g.Cp; t.p = g.p; t.h = g.h; t.s = g.s; t.K = g.K;
@@ -1344,11 +1388,18 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     t.HL = t.f32 ? g.L : g.K;
     const int nplanes = t.f32 ? 2 : 1;
     // float32 lists in registers use 32-bit keys when the window index fits
-    // 12 bits (window <= 63): up to 2^-11 relative rounding of the pool
+    // 12 bits (window <= 63): up to 2^(bits-23) relative rounding of the pool
     // scores.  Pools over 32 (the shared-memory heap) keep 64-bit keys when
     // they fit -- the rounding widens the re-rank's band, which for K 70 at
-    // window 61 sent a quarter of the references to a window recompute --
-    // and take 32-bit keys (half the heap) only when nothing else fits.
+    // window 61 sent a quarter of the references to a window recompute -- and
+    // take 32-bit keys (half the heap) when nothing else fits.  Column parts
+    // cost selection work (each part fills its own list), so at 11 window-
+    // index bits the fewest parts come first whatever the keys; at 12 bits
+    // (2^-11 rounding) 64-bit keys come first, with more parts if need be.
+    // Measured on four-channel float32, K 70 (matching plus re-rank):
+    // window 39, one part with 32-bit keys 17.2 M references/s against 14.8
+    // for two parts with 64-bit keys; window 61, p 7: three parts with
+    // 64-bit keys 7.3 M/s against 6.2 for two parts with 32-bit keys.
     int tb32 = 0;
     if (t.f32 && !t.ncc) {  // NCC: exact scores (its scores cluster near the top)
         const int ww = 2 * g.h + 1;
@@ -1358,19 +1409,24 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     }
     t.tbits = t.HL <= 32 ? tb32 : 0;
     const TcGeom t0 = t;
-    for (int keys = 0; keys < 2; ++keys) {
+    const bool keys_first = tb32 >= 12;
+    for (int it = 0; it < 2 * kMaxSplit; ++it) {
+    const int keys = keys_first ? it / kMaxSplit : it & 1;
+    const int xs = keys_first ? it % kMaxSplit + 1 : (it >> 1) + 1;
+    if (xs > 1 && t0.ncc) continue;
+    t = t0;
     if (keys == 1) {
-        if (t.HL <= 32 || !tb32) break;
-        t = t0;
+        if (t.HL <= 32 || !tb32) continue;
         t.tbits = tb32;
     }
+    t.xs = xs;
     // lane -> reference mapping: rr reference rows x rc columns per warp, a
     // wgy x wgx grid of 4 warps
     static const int kMaps[6][2] = {{8, 2}, {16, 4}, {32, 4}, {8, 4}, {4, 4}, {1, 1}};
     // A in shared memory first; classes where nothing fits (the staged tile
     // plus A beyond 227 KB: float32 with four channels, large windows) keep
     // A in tensor memory instead (TS MMAs), beside narrower accumulators
-    for (int ts = 0; ts <= 1; ++ts)
+    for (int ts = xs > 1 ? 1 : 0; ts <= 1; ++ts)
     for (int ns = 2; ns >= 1; --ns) {
         if (ns == 2 && t.HL > 32) continue;
         const int a_cols = ts ? nplanes * t.nkc * 4 : 0;  // 16-bit elements, two per column
@@ -1390,15 +1446,19 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
                     const int nx_max = (c.tx - 1) * g.s + 2 * g.h + 1;
                     c.Rb = (nr_max + g.p_eff - 1 + 15) / 16 * 16;
                     if (c.Rb > bufcols) continue;
+                    c.kcols = bufcols / c.Rb;
+                    // candidate columns one staged tile covers: the union, or
+                    // the largest column part of it
+                    const int nch = (nx_max + c.kcols - 1) / c.kcols;
+                    const int cols = std::min(nx_max, (nch + xs - 1) / xs * c.kcols);
                     // staged row: alignment slack + every candidate column's patch row;
                     // an odd 16-byte chunk count keeps 16-byte row reads conflict-free
-                    c.nc_box = ((7 + (nx_max - 1) * g.Cp + 8 * g.pw + 7) / 8) | 1;
+                    c.nc_box = ((7 + (cols - 1) * g.Cp + 8 * g.pw + 7) / 8) | 1;
                     if (c.nc_box > 255) continue;
                     c.nslots = ns;
                     c.bufcols = bufcols;
                     c.nst = nst;
                     c.kbuf = kbuf;
-                    c.kcols = bufcols / c.Rb;
                     c.base_pitch = c.nc_box * 16;
                     c.base_bytes = c.Rb * c.base_pitch;
                     c.qpitch = (c.kcols * c.Rb + g.p_eff + 16) * 16;
@@ -1444,7 +1504,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
             return true;
         }
     }
-    }  // keys
+    }  // (keys, xs)
     return false;
 }
 
@@ -1515,6 +1575,9 @@ bool make_job(TcJob& j, const Geom& g, const TcGeom& t, const TcArgs& a, int til
     j = TcJob{};
     if (!encode_plane(&j.map[0], a.plane0, g, t)) return false;
     if (t.f32 && !encode_plane(&j.map[1], a.plane1, g, t)) return false;
+    j.plane[0] = a.plane0;
+    j.plane[1] = a.plane1;
+    j.pitch = g.plane_pitch;
     j.nsp = a.nsp;
     j.nrm = a.nrm;
     j.out_idx = a.out_idx;
@@ -1632,6 +1695,11 @@ int tc_num_choices(const Geom& g) {
     return make_tc_geom(g, t, -1, &n) ? n * kSplitChoices : 0;
 }
 
+int tc_column_parts(const Geom& g) {
+    TcGeom t{};
+    return make_tc_geom(g, t) ? t.xs : 1;
+}
+
 int tc_score_bits(const Geom& g) {
     TcGeom t{};
     return make_tc_geom(g, t) ? t.tbits : 0;
@@ -1684,7 +1752,11 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
             J.tile_begin = tiles;
             const int jt = J.tiles_x * ((J.n_ry + P.g.ty - 1) / P.g.ty);
             const int room = (a.split_idx && a.split_val) ? a.wsplit : 1;
-            const int w = split ? split_cap(gs[first + j], P.g, wsel > 0 ? std::min(wsel, room) : room) : 1;
+            int w = split ? split_cap(gs[first + j], P.g, wsel > 0 ? std::min(wsel, room) : room) : 1;
+            if (P.g.xs > 1) {  // column parts: always that many parts
+                if (room < P.g.xs) return cudaErrorInvalidValue;
+                w = P.g.xs;
+            }
             if (w > 1) {
                 J.wsplit = w;
                 MergeJob& m = M.jobs[M.njobs++];
@@ -1725,6 +1797,7 @@ cudaError_t launch_tc_batch(const Geom* gs, const TcArgs* as, int n, cudaStream_
 int tc_window_split(const Geom& g) {
     TcGeom t{};
     if (!make_tc_geom(g, t)) return 1;
+    if (t.xs > 1) return t.xs;
     const long long items = (long long)((g.n_rx + t.tx - 1) / t.tx) * ((g.n_ry + t.ty - 1) / t.ty);
     const long long want = kSplitTarget;
     int cap = 1;

@@ -75,5 +75,11 @@ def test_workspace_bytes_query():
                  (64, 64, 1, B.BM_U8, 8, 21, 1, 16)]:
         ws = B.bm_workspace_bytes(*args)
         assert ws >= B.bm_static_scratch_bytes(*args) - 256 > 0
-    assert B.bm_workspace_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 0  # direct kernel
+    assert B.bm_workspace_bytes(160, 150, 4, B.BM_U8, 8, 127, 4, 128) == 0  # direct kernel
+    # column parts (the staged tile fits only per part): 2 parts, their lists included
+    assert B.bm_window_split(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 2
+    assert B.bm_workspace_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) > 0
+    assert B.bm_window_split(512, 512, 4, B.BM_F32, 8, 61, 3, 32) == 2
+    assert B.bm_static_scratch_bytes(512, 512, 4, B.BM_F32, 8, 61, 3, 32) > \
+        B.bm_static_scratch_bytes(512, 512, 4, B.BM_F32, 8, 61, 3, 16)
     assert B.bm_workspace_bytes(64, 64, 1, B.BM_U8, 8, 22, 1, 16) == 0      # invalid

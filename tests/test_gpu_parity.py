@@ -248,6 +248,59 @@ def test_tensor_memory_a_classes(ctx, case):
     compare(img, p, win, s, K, gidx, gdist, threads=0)
 
 
+COLUMN_PART_CASES = [
+    # classes whose staged tile fits only when each tile's candidate columns
+    # are split into contiguous parts, each staging its own columns (and A
+    # read from global memory); id, shape, parts the class uses
+    ("cp_f32_c4_p8_w61_k32", 110, 97, 4, "f32", 8, 61, 3, 32, 2),
+    ("cp_f32_c4_p8_w61_k70", 104, 99, 4, "f32", 8, 61, 3, 70, 2),
+    ("cp_f32_c4_p7_w61_k16", 131, 125, 4, "f32", 7, 61, 4, 16, 2),
+    ("cp_f32_c4_p7_w61_k70", 120, 111, 4, "f32", 7, 61, 4, 70, 3),
+    ("cp_f32_c4_w61_k128_heap32", 100, 96, 4, "f32", 8, 61, 3, 128, 2),   # 32-bit-key heap
+    ("cp_f32_c4_w81_3parts", 90, 84, 4, "f32", 8, 81, 3, 32, 3),
+    ("cp_one_column", 70, 8, 4, "f32", 8, 61, 3, 32, 2),   # one candidate column: a part is empty
+    ("cp_narrow", 60, 12, 4, "f32", 7, 61, 4, 32, 2),
+]
+
+
+@pytest.mark.parametrize("case", COLUMN_PART_CASES, ids=[c[0] for c in COLUMN_PART_CASES])
+def test_column_part_classes(ctx, case):
+    name, H, W, C, dt, p, win, s, K, parts = case
+    code = B.BM_U8 if dt == "u8" else B.BM_F32
+    assert B.bm_workspace_bytes(H, W, C, code, p, win, s, K) > 0  # the tensor-core path
+    assert B.bm_window_split(H, W, C, code, p, win, s, K) == parts
+    img = make_image(H, W, C, dt, seed=zlib.crc32(name.encode()) % 10007, sigma=20.0)
+    before = ctx.stats()["tc_jobs"]
+    gidx, gdist = run(ctx, img, p, win, s, K, "selfconv")
+    assert ctx.stats()["tc_jobs"] == before + 1
+    compare(img, p, win, s, K, gidx, gdist, threads=0)
+
+
+def test_column_parts_in_a_batch(ctx):
+    """Jobs of a column-part class in one batch with others (uneven sizes):
+    each equals the same job alone."""
+    specs = [(110, 97, 4, "f32", 8, 61, 3, 32), (64, 70, 4, "f32", 8, 61, 3, 32),
+             (100, 90, 1, "f32", 8, 39, 3, 16), (200, 41, 4, "f32", 8, 61, 3, 32),
+             (96, 96, 4, "f32", 7, 61, 4, 70)]
+    imgs, outs, reqs = [], [], []
+    for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
+        t = torch.from_numpy(make_image(H, W, C, dt, seed=700 + i, sigma=20.0)).cuda()
+        idx, dist = ctx.outputs(t, p, s, K)
+        imgs.append(t)
+        outs.append((idx, dist))
+        reqs.append(B.Context.request(t, p, win, s, K, idx, dist))
+    ctx.match_batch(reqs, stream=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    for (H, W, C, dt, p, win, s, K), t, (idx, dist) in zip(specs, imgs, outs):
+        a_idx, a_dist = ctx.match(t, p, win, s, K)
+        torch.cuda.synchronize()
+        assert torch.equal(a_idx, idx) and torch.equal(a_dist, dist)
+    H, W, C, dt, p, win, s, K = specs[3]
+    ny, nx = B.bm_num_refs(H, W, p, s)
+    compare(make_image(H, W, C, dt, seed=703, sigma=20.0), p, win, s, K, outs[3][0].cpu().numpy(),
+            outs[3][1].cpu().numpy(), refs=sample_refs(ny, nx, 80, 704))
+
+
 def test_selfconv_equals_direct_bitwise_on_u8(ctx):
     img = make_image(200, 180, 1, "u8", seed=5)
     a = run(ctx, img, 8, 39, 3, 16, "selfconv")

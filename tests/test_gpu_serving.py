@@ -176,7 +176,7 @@ def test_mixed_class_batch_graph_replay():
     specs = [(100, 90, 1, "f32", 8, 39, 3, 16), (64, 64, 1, "u8", 8, 21, 1, 16),
              (80, 72, 4, "u8", 8, 39, 3, 32), (150, 133, 1, "f32", 7, 61, 4, 70),
              (96, 96, 1, "u8", 7, 39, 4, 32),
-             (90, 84, 4, "f32", 8, 61, 3, 32)]  # a direct-kernel class: its own branch
+             (90, 84, 4, "f32", 8, 127, 3, 128)]  # a direct-kernel class: its own branch
     imgs, outs, reqs = [], [], []
     for i, (H, W, C, dt, p, win, s, K) in enumerate(specs):
         t = torch.from_numpy(_image(H, W, C, dt, 300 + i)).cuda()
@@ -184,6 +184,7 @@ def test_mixed_class_batch_graph_replay():
         imgs.append(t)
         outs.append(o)
         reqs.append(ctx.request(t, p, win, s, K, o[0], o[1]))
+    assert B.bm_workspace_bytes(90, 84, 4, B.BM_F32, 8, 127, 3, 128) == 0  # direct kernel
     torch.cuda.synchronize()
     for rnd in range(2):
         if rnd == 1:

@@ -105,17 +105,20 @@ def test_static_rejects_jobs_beyond_the_scratch():
 
 
 def test_direct_path_geometry_needs_only_the_header():
-    # window 127 with K 128 is outside the tensor-core kernel's tiling (its
-    # staged candidate rows exceed one TMA box): only the 256-byte header
-    assert B.bm_static_scratch_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 256
+    # four channels at window 127 with K 128 are outside the tensor-core
+    # kernel's tiling (even a quarter of the staged tile exceeds shared
+    # memory): only the 256-byte header
+    assert B.bm_static_scratch_bytes(160, 150, 4, B.BM_U8, 8, 127, 4, 128) == 256
 
 
 @pytest.mark.gpu
 def test_static_allocates_nothing_and_covers_direct_and_four_channels():
     """After a warm-up call, further calls leave free device memory unchanged.
 
-    Covers a 4-channel uint8 job (tensor cores), a float32 job and a
-    geometry that takes the direct kernel, each compared with bm_match.
+    Covers a 4-channel uint8 job (tensor cores), a float32 job, a 4-channel
+    float32 class that runs in column parts (part lists in the scratch, a
+    merge launch) and a geometry that takes the direct kernel, each compared
+    with bm_match.
     """
     import torch
 
@@ -124,9 +127,12 @@ def test_static_allocates_nothing_and_covers_direct_and_four_channels():
     jobs = [
         (synth.rgbnir(200, 180, 20.0, 7101), 8, 39, 3, 32),            # u8, C 4
         (synth.gray(256, 240, 25.0, 7102, np.float32), 8, 39, 3, 16),  # f32, C 1
-        (synth.gray(160, 150, 20.0, 7103, np.uint8), 8, 127, 4, 128),  # direct kernel
+        (synth.rgbnir(160, 150, 20.0, 7103), 8, 127, 4, 128),            # direct kernel
+        (np.stack([synth.gray(120, 110, 20.0, 7105 + c, np.float32) for c in range(4)], -1),
+         8, 61, 3, 32),                                                  # f32, C 4, column parts
     ]
-    assert B.bm_static_scratch_bytes(160, 150, 1, B.BM_U8, 8, 127, 4, 128) == 256
+    assert B.bm_static_scratch_bytes(160, 150, 4, B.BM_U8, 8, 127, 4, 128) == 256
+    assert B.bm_window_split(120, 110, 4, B.BM_F32, 8, 61, 3, 32) == 2
     ctx = B.Context(0)
     st = torch.cuda.current_stream()
     data = []
