@@ -44,6 +44,7 @@
 #include "bm_internal.h"
 
 #include <climits>
+#include <type_traits>
 
 namespace bm {
 namespace {
@@ -90,6 +91,16 @@ struct PairSrc {
     }
     __device__ __forceinline__ static float elem(const float2* row, int e) { return row[e].x; }
 };
+// QuadSrc: a region in shared memory stored plainly, for C a multiple of 4:
+// every patch row starts on a 16-byte boundary and is read as float4.
+struct QuadSrc {
+    const float* base;
+    int y0, x0, pitch, C;
+    __device__ __forceinline__ const float* at(int y, int x) const {
+        return base + (y - y0) * pitch + (x - x0) * C;
+    }
+    __device__ __forceinline__ static float elem(const float* row, int e) { return row[e]; }
+};
 // PlainSrc: the image in global memory, or the norms region.
 struct PlainSrc {
     const float* base;
@@ -135,6 +146,35 @@ __device__ __forceinline__ float direct_f32(const PairSrc& X, int p_rt, int C_rt
     }
     return ((__uint_as_float((unsigned)acc[0]) + __uint_as_float((unsigned)(acc[0] >> 32))) +
             (__uint_as_float((unsigned)acc[1]) + __uint_as_float((unsigned)(acc[1] >> 32)))) + tail;
+}
+
+// The same sum from a QuadSrc region: four elements per 16-byte load, two
+// packed subtract / fused multiply-add pairs, four running sums.
+template <int FP = 0, int FC = 0>
+__device__ __forceinline__ float direct_f32(const QuadSrc& X, int p_rt, int C_rt, const float* ref,
+                                            int yc, int xc) {
+    const int p = FP ? FP : p_rt, C = FC ? FC : C_rt;
+    const int nq = (p * C) >> 2;  // float4 per patch row
+    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+    const float* cbase = X.at(yc, xc);
+#pragma unroll
+    for (int u = 0; u < p; ++u) {
+        const float4* crow = reinterpret_cast<const float4*>(cbase + u * X.pitch);
+        const float4* rrow = reinterpret_cast<const float4*>(ref + u * X.pitch);
+#pragma unroll 4
+        for (int t = 0; t < nq; ++t) {
+            const float4 a = rrow[t], b = crow[t];
+            unsigned long long d0, d1;
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(f2_bits(make_float2(a.x, a.y))), "l"(f2_bits(make_float2(b.x, b.y))));
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(f2_bits(make_float2(a.z, a.w))), "l"(f2_bits(make_float2(b.z, b.w))));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[2 * (u & 1)]) : "l"(d0));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc[2 * (u & 1) + 1]) : "l"(d1));
+        }
+    }
+    auto lo = [](unsigned long long v) { return __uint_as_float((unsigned)v); };
+    auto hi = [](unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); };
+    return ((lo(acc[0]) + hi(acc[0])) + (lo(acc[1]) + hi(acc[1]))) +
+           ((lo(acc[2]) + hi(acc[2])) + (lo(acc[3]) + hi(acc[3])));
 }
 
 // The same sum elementwise in order (global-memory source).
@@ -397,8 +437,10 @@ __device__ bool rerank_ref(const RerankParams& P, const RerankJob& J, const Src&
         key[i] = kNone;
         if (member[i]) {
             float d32;
-            if constexpr (sizeof(T) == sizeof(float2)) d32 = direct_f32<FP, FC>(X, P.p, P.C, ref, yc[i], xc[i]);
-            else d32 = direct_f32(X, P.p, P.C, ref, yc[i], xc[i]);
+            if constexpr (!std::is_same<Src, PlainSrc>::value)
+                d32 = direct_f32<FP, FC>(X, P.p, P.C, ref, yc[i], xc[i]);
+            else
+                d32 = direct_f32(X, P.p, P.C, ref, yc[i], xc[i]);
             key[i] = ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)pool.off[i];
             // identity estimate d~ = n_r - 2 (v - eps n_j) against its bound 2 eps (n_r + n_j)
             const float dt = nr - 2.0f * (v[i] - kEps * nc[i]);
@@ -531,8 +573,11 @@ __device__ __forceinline__ int tile_job(const RerankParams& P, int t) {
 }
 
 // FP, FC: patch side and channels fixed at compile time (0: from P).
-template <int S, int FP, int FC>
+// kQuad: the region stored plainly (C a multiple of 4), else as element pairs.
+template <int S, int FP, int FC, bool kQuad>
 __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
+    using Src = typename std::conditional<kQuad, QuadSrc, PairSrc>::type;
+    using T = typename std::conditional<kQuad, float, float2>::type;
     extern __shared__ __align__(16) float2 sm2[];
     __shared__ unsigned long long list_s[kFbSlots * 32];  // overflow: window keys, then a list
     __shared__ unsigned long long ovf_u[kMaxTileRefs];
@@ -560,12 +605,17 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
     const int irows = iy1 - iy0 + 1, nrows = ny1 - iy0 + 1;
     for (int y = warp; y < irows; y += kTileWarps) {
         const float* g = J.img + ((size_t)(iy0 + y) * J.W + ix0) * P.C;
-        for (int e0 = 0; e0 < ipitch; e0 += 32) {
-            const int e = e0 + lane;
-            const float a = e < ipitch ? __ldg(g + e) : 0.f;
-            float b = __shfl_down_sync(0xffffffffu, a, 1);
-            if (lane == 31) b = e + 1 < ipitch ? __ldg(g + e + 1) : 0.f;
-            if (e < ipitch) simg[y * ipitch + e] = make_float2(a, b);
+        if constexpr (kQuad) {
+            float* row = reinterpret_cast<float*>(sm2) + y * ipitch;
+            for (int e = lane; e < ipitch; e += 32) row[e] = __ldg(g + e);
+        } else {
+            for (int e0 = 0; e0 < ipitch; e0 += 32) {
+                const int e = e0 + lane;
+                const float a = e < ipitch ? __ldg(g + e) : 0.f;
+                float b = __shfl_down_sync(0xffffffffu, a, 1);
+                if (lane == 31) b = e + 1 < ipitch ? __ldg(g + e + 1) : 0.f;
+                if (e < ipitch) simg[y * ipitch + e] = make_float2(a, b);
+            }
         }
     }
     for (int y = warp; y < nrows; y += kTileWarps) {
@@ -573,7 +623,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
         for (int x = lane; x < npitch; x += 32) snrm[y * npitch + x] = __ldg(g + x);
     }
     __syncthreads();
-    const PairSrc X{simg, iy0, ix0, ipitch, P.C};
+    const Src X{reinterpret_cast<const T*>(sm2), iy0, ix0, ipitch, P.C};
     const PlainSrc N{snrm, iy0, ix0, npitch, 1};
     // references i = warp + 8 m, row-major in the tile: (qi, ri) = divmod(i, ncols)
     int qi = warp / ncols, ri = warp % ncols;
@@ -587,7 +637,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
         }
         if (i + kTileWarps < nref) pool.load(P, J, (size_t)(ry0 + qi) * J.n_rx + rx0 + ri, lane);
         unsigned long long U;
-        if (rerank_ref<S, PairSrc, float2, FP, FC>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
+        if (rerank_ref<S, Src, T, FP, FC>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
             const int o = atomicAdd(&ovf_n, 1);
             ovf_ref[o] = i;
             ovf_u[o] = U;
@@ -604,7 +654,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
             atomicAdd(P.counters + 0, 1ull);
         }
         __syncthreads();
-        window_filter<PairSrc, float2>(P, J, X, ry, rx, warp, kTileWarps, lane, ovf_u[o], list_s, &cand_n);
+        window_filter<Src, T>(P, J, X, ry, rx, warp, kTileWarps, lane, ovf_u[o], list_s, &cand_n);
         __syncthreads();
         const int n = cand_n;
         if (warp == 0) {
@@ -618,8 +668,8 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
                                            (size_t)ry * J.n_rx + rx);
             } else {
                 // more ties than the buffer holds: the exact top-(K+1) by insertion
-                window_part<PairSrc, float2>(P, J, X, ry, rx, 0, 1, lane, list_s);
-                write_list<PairSrc, float2>(P, J, X, ry, rx, lane, list_s);
+                window_part<Src, T>(P, J, X, ry, rx, 0, 1, lane, list_s);
+                write_list<Src, T>(P, J, X, ry, rx, lane, list_s);
             }
         }
         __syncthreads();
@@ -647,13 +697,17 @@ __global__ void __launch_bounds__(128) rerank_global_kernel(const __grid_constan
     }
 }
 
+// Region layout: plain (16-byte patch rows) when C is a multiple of 4.
+bool quad_layout(const Geom& g) { return g.C % 4 == 0; }
+
 // Tile shape and shared memory for a class; false: no region fits.
 bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
     static const int kShapes[5][2] = {{8, 8}, {4, 8}, {4, 4}, {2, 2}, {1, 1}};
     for (const auto& sh : kShapes) {
         const int rows = (sh[0] - 1) * g.s + 2 * g.h + g.p;
         const int cols = (sh[1] - 1) * g.s + 2 * g.h + g.p;
-        img_cap = (rows * cols * g.C + 1) / 2 * 2;  // element pairs (8 B each)
+        // capacity in 8-byte units: element pairs, or two plain elements
+        img_cap = quad_layout(g) ? (rows * cols * g.C + 1) / 2 : (rows * cols * g.C + 1) / 2 * 2;
         smem = img_cap * 8 + (rows - g.p + 1) * (cols - g.p + 1) * 4;
         if (smem <= kTileSmemLimit) {
             TRY = sh[0];
@@ -666,12 +720,13 @@ bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
 
 template <int S>
 cudaError_t launch_s(const RerankParams& P, bool tiled, int smem, int grid, cudaStream_t st) {
-    if (tiled && P.p == 8 && P.C == 1) {  // the 8 x 8 grey patch, unrolled
-        cudaFuncSetAttribute(rerank_tile_kernel<S, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        rerank_tile_kernel<S, 8, 1><<<grid, kTileWarps * 32, smem, st>>>(P);
-    } else if (tiled) {
-        cudaFuncSetAttribute(rerank_tile_kernel<S, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        rerank_tile_kernel<S, 0, 0><<<grid, kTileWarps * 32, smem, st>>>(P);
+    void (*kern)(RerankParams) = nullptr;
+    if (tiled && P.p == 8 && P.C == 1) kern = rerank_tile_kernel<S, 8, 1, false>;  // 8 x 8 grey, unrolled
+    else if (tiled && P.C % 4 == 0) kern = rerank_tile_kernel<S, 0, 0, true>;
+    else if (tiled) kern = rerank_tile_kernel<S, 0, 0, false>;
+    if (kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        kern<<<grid, kTileWarps * 32, smem, st>>>(P);
     } else {
         rerank_global_kernel<S><<<grid, 128, 0, st>>>(P);
     }
