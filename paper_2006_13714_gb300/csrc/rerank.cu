@@ -722,6 +722,7 @@ template <int S>
 cudaError_t launch_s(const RerankParams& P, bool tiled, int smem, int grid, cudaStream_t st) {
     void (*kern)(RerankParams) = nullptr;
     if (tiled && P.p == 8 && P.C == 1) kern = rerank_tile_kernel<S, 8, 1, false>;  // 8 x 8 grey, unrolled
+    else if (tiled && P.p == 8 && P.C == 4 && S <= 3) kern = rerank_tile_kernel<(S <= 3 ? S : 1), 8, 4, true>;
     else if (tiled && P.C % 4 == 0) kern = rerank_tile_kernel<S, 0, 0, true>;
     else if (tiled) kern = rerank_tile_kernel<S, 0, 0, false>;
     if (kern) {
