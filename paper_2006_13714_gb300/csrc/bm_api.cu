@@ -28,6 +28,37 @@ namespace bm {
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Float32 pool L: the candidates per reference the tensor-core pass keeps for
+// the re-rank.  A reference whose whole pool lies inside the re-rank's error
+// band is recomputed over its window (every candidate's direct distance), so
+// the pool needs room beyond K for the candidates whose estimates fall
+// within the error of the K-th.  L = K + 8 (rounded up to 8) by default; a
+// larger pool costs selection work in the tensor-core pass (a looser
+// threshold, more appends) and pays where that recompute is frequent:
+// - four or eight channels: K + 16 up to K 40, K + 24 above;
+// - one to three channels at windows of 45 or more: K + 16 for K <= 24
+//   (32 entries: the register lists' full width) and for K > 40.
+// Measured recompute rates at L = K + 8 (1024^2 images): four-channel K 70
+// 8-15 %, window 61 K 16 5 %, one-channel window 61 K 70 8 %; at K + 16/24
+// under 0.3 %.  Times (1024^2, float32, matching plus re-rank): four-channel
+// p 8 window 61 K 70 15.3 -> 9.9 ms, K 16 6.1 -> 3.8 ms; one-channel window
+// 61 K 16 1.65 -> 1.16 ms.  On the 512^2 window-39 K 16 batch the larger pool
+// cost 9 % (recomputes were 0.35 %), so it stays at K + 8 there.
+static int pool_extra(int K, int C, int h) {
+    if (C >= 4) return K <= 40 ? 16 : 24;
+    if (2 * h + 1 >= 45 && (K <= 24 || K > 40)) return 16;
+    return 8;
+}
+
+// The larger pool is taken only when its tensor-core geometry is no worse in
+// any of these: no more column parts, no fewer tile slots or candidate
+// columns per MMA, no smaller append buffer (16 entries merge after every
+// block), A not moved to tensor memory, the same tile shape.
+static bool no_worse(const TcShape& b, const TcShape& a) {
+    return b.xs <= a.xs && b.ns >= a.ns && b.kcols >= a.kcols && b.kbuf >= a.kbuf && b.ts <= a.ts &&
+           b.ty == a.ty && b.tx == a.tx;
+}
+
 int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, int K) {
     if (H < 1 || W < 1 || C < 1 || C > kMaxC || p < 1 || p > H || p > W) return BM_ERR_INVALID;
     if (win < 1 || (win % 2) == 0 || win > kMaxWindow || s < 1 || K < 1 || K > kMaxK)
@@ -51,6 +82,16 @@ int make_geom(Geom& g, int H, int W, int C, int dtype, int p, int win, int s, in
     g.plane_pitch = round_up(W * g.Cp + 8 * g.pw + 16, 8);
     g.plane_rows = H + g.p_eff + 8;
     g.L = dtype == kF32 ? std::min(160, round_up(K + 8, 8)) : 0;
+    if (dtype == kF32) {
+        // a larger pool where references often fall to a window recompute
+        const int extra = pool_extra(K, C, g.h);
+        if (extra > 8) {
+            Geom big = g;
+            big.L = std::min(160, round_up(K + extra, 8));
+            TcShape a{}, b{};
+            if (big.L > g.L && tc_shape(g, a) && tc_shape(big, b) && no_worse(b, a)) g.L = big.L;
+        }
+    }
     return BM_OK;
 }
 

@@ -198,6 +198,13 @@ int tc_window_split(const Geom& g);
 // Column parts of the job's class (1: none).  Above 1 the job always runs
 // split in that many parts and needs the part-list room.
 int tc_column_parts(const Geom& g);
+// Shape of the tensor-core geometry a job gets (column parts, A in tensor
+// memory, tile slots, tile rows x columns, candidate columns per MMA,
+// append-buffer entries); false if the job runs on the direct kernel.
+struct TcShape {
+    int xs, ts, ns, ty, tx, kcols, kbuf;
+};
+bool tc_shape(const Geom& g, TcShape& s);
 
 // (a6) float32 boundary re-rank: direct recomputation of the pool's band,
 // FP64 only for ties at the K-th boundary; writes the final outputs.

@@ -1395,7 +1395,9 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     // take 32-bit keys (half the heap) when nothing else fits.  Column parts
     // cost selection work (each part fills its own list), so at 11 window-
     // index bits the fewest parts come first whatever the keys; at 12 bits
-    // (2^-11 rounding) 64-bit keys come first, with more parts if need be.
+    // (2^-11 rounding) 64-bit keys come first, with more parts if need be --
+    // unless the pool has 24 or more entries beyond K, which absorb the
+    // rounding (then the fewest parts come first again).
     // Measured on four-channel float32, K 70 (matching plus re-rank):
     // window 39, one part with 32-bit keys 17.2 M references/s against 14.8
     // for two parts with 64-bit keys; window 61, p 7: three parts with
@@ -1409,7 +1411,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
     }
     t.tbits = t.HL <= 32 ? tb32 : 0;
     const TcGeom t0 = t;
-    const bool keys_first = tb32 >= 12;
+    const bool keys_first = tb32 >= 12 && g.L - g.K < 24;
     for (int it = 0; it < 2 * kMaxSplit; ++it) {
     const int keys = keys_first ? it / kMaxSplit : it & 1;
     const int xs = keys_first ? it % kMaxSplit + 1 : (it >> 1) + 1;
@@ -1437,7 +1439,7 @@ bool make_tc_geom(const Geom& g, TcGeom& t, int choice = -1, int* nchoices = nul
         TcGeom bestc{};
         int ncand = 0;
         for (const auto& mp : kMaps)
-            for (int kbuf = 32; kbuf >= 16; kbuf -= 16)
+            for (int kbuf = 32; kbuf >= 16; kbuf -= 8)
                 for (int nst = kMaxSt; nst >= 2; --nst) {
                     TcGeom c = t;
                     const int rr = mp[0], wgx = mp[1], rc = 32 / rr, wgy = 4 / wgx;
@@ -1693,6 +1695,13 @@ int tc_num_choices(const Geom& g) {
     TcGeom t{};
     int n = 0;
     return make_tc_geom(g, t, -1, &n) ? n * kSplitChoices : 0;
+}
+
+bool tc_shape(const Geom& g, TcShape& s) {
+    TcGeom t{};
+    if (!make_tc_geom(g, t)) return false;
+    s = TcShape{t.xs, t.ts, t.nslots, t.ty, t.tx, t.kcols, t.kbuf};
+    return true;
 }
 
 int tc_column_parts(const Geom& g) {

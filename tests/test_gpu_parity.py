@@ -255,7 +255,7 @@ COLUMN_PART_CASES = [
     ("cp_f32_c4_p8_w61_k32", 110, 97, 4, "f32", 8, 61, 3, 32, 2),
     ("cp_f32_c4_p8_w61_k70", 104, 99, 4, "f32", 8, 61, 3, 70, 2),
     ("cp_f32_c4_p7_w61_k16", 131, 125, 4, "f32", 7, 61, 4, 16, 2),
-    ("cp_f32_c4_p7_w61_k70", 120, 111, 4, "f32", 7, 61, 4, 70, 3),
+    ("cp_f32_c4_p7_w61_k70", 120, 111, 4, "f32", 7, 61, 4, 70, 2),   # pool K + 24, 32-bit keys
     ("cp_f32_c4_w61_k128_heap32", 100, 96, 4, "f32", 8, 61, 3, 128, 2),   # 32-bit-key heap
     ("cp_f32_c4_w81_3parts", 90, 84, 4, "f32", 8, 81, 3, 32, 3),
     ("cp_one_column", 70, 8, 4, "f32", 8, 61, 3, 32, 2),   # one candidate column: a part is empty
