@@ -574,8 +574,9 @@ __device__ __forceinline__ int tile_job(const RerankParams& P, int t) {
 
 // FP, FC: patch side and channels fixed at compile time (0: from P).
 // kQuad: the region stored plainly (C a multiple of 4), else as element pairs.
-template <int S, int FP, int FC, bool kQuad>
-__global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
+// NW: warps per block (16 where the region leaves room for at most two blocks per SM).
+template <int S, int FP, int FC, bool kQuad, int NW = kTileWarps>
+__global__ void __launch_bounds__(NW * 32) rerank_tile_kernel(const __grid_constant__ RerankParams P) {
     using Src = typename std::conditional<kQuad, QuadSrc, PairSrc>::type;
     using T = typename std::conditional<kQuad, float, float2>::type;
     extern __shared__ __align__(16) float2 sm2[];
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
     float2* simg = sm2;
     float* snrm = reinterpret_cast<float*>(sm2 + P.img_cap);
     const int irows = iy1 - iy0 + 1, nrows = ny1 - iy0 + 1;
-    for (int y = warp; y < irows; y += kTileWarps) {
+    for (int y = warp; y < irows; y += NW) {
         const float* g = J.img + ((size_t)(iy0 + y) * J.W + ix0) * P.C;
         if constexpr (kQuad) {
             float* row = reinterpret_cast<float*>(sm2) + y * ipitch;
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
             }
         }
     }
-    for (int y = warp; y < nrows; y += kTileWarps) {
+    for (int y = warp; y < nrows; y += NW) {
         const float* g = J.nrm + (size_t)(iy0 + y) * J.Wc + ix0;
         for (int x = lane; x < npitch; x += 32) snrm[y * npitch + x] = __ldg(g + x);
     }
@@ -627,15 +628,15 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
     const PlainSrc N{snrm, iy0, ix0, npitch, 1};
     // references i = warp + 8 m, row-major in the tile: (qi, ri) = divmod(i, ncols)
     int qi = warp / ncols, ri = warp % ncols;
-    for (int i = warp; i < nref; i += kTileWarps) {
+    for (int i = warp; i < nref; i += NW) {
         const PoolRegs<S> cur = pool;
         const int ry = ry0 + qi, rx = rx0 + ri;
-        ri += kTileWarps;
+        ri += NW;
         while (ri >= ncols) {
             ri -= ncols;
             ++qi;
         }
-        if (i + kTileWarps < nref) pool.load(P, J, (size_t)(ry0 + qi) * J.n_rx + rx0 + ri, lane);
+        if (i + NW < nref) pool.load(P, J, (size_t)(ry0 + qi) * J.n_rx + rx0 + ri, lane);
         unsigned long long U;
         if (rerank_ref<S, Src, T, FP, FC>(P, J, X, N, ry, rx, lane, cur, U) && lane == 0) {
             const int o = atomicAdd(&ovf_n, 1);
@@ -654,7 +655,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rerank_tile_kernel(const __gr
             atomicAdd(P.counters + 0, 1ull);
         }
         __syncthreads();
-        window_filter<Src, T>(P, J, X, ry, rx, warp, kTileWarps, lane, ovf_u[o], list_s, &cand_n);
+        window_filter<Src, T>(P, J, X, ry, rx, warp, NW, lane, ovf_u[o], list_s, &cand_n);
         __syncthreads();
         const int n = cand_n;
         if (warp == 0) {
@@ -721,13 +722,19 @@ bool tile_shape(const Geom& g, int& TRY, int& TRX, int& img_cap, int& smem) {
 template <int S>
 cudaError_t launch_s(const RerankParams& P, bool tiled, int smem, int grid, cudaStream_t st) {
     void (*kern)(RerankParams) = nullptr;
+    // four-channel regions over a quarter of the shared memory fit at most two
+    // blocks per SM: those blocks take 16 warps instead of 8 (pools up to 96)
+    constexpr int S3 = S <= 3 ? S : 1;
+    const bool wide = tiled && P.C % 4 == 0 && S <= 3 && smem > kTileSmemLimit / 4;
     if (tiled && P.p == 8 && P.C == 1) kern = rerank_tile_kernel<S, 8, 1, false>;  // 8 x 8 grey, unrolled
-    else if (tiled && P.p == 8 && P.C == 4 && S <= 3) kern = rerank_tile_kernel<(S <= 3 ? S : 1), 8, 4, true>;
+    else if (wide && P.p == 8 && P.C == 4) kern = rerank_tile_kernel<S3, 8, 4, true, 16>;
+    else if (wide) kern = rerank_tile_kernel<S3, 0, 0, true, 16>;
+    else if (tiled && P.p == 8 && P.C == 4 && S <= 3) kern = rerank_tile_kernel<S3, 8, 4, true>;
     else if (tiled && P.C % 4 == 0) kern = rerank_tile_kernel<S, 0, 0, true>;
     else if (tiled) kern = rerank_tile_kernel<S, 0, 0, false>;
     if (kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        kern<<<grid, kTileWarps * 32, smem, st>>>(P);
+        kern<<<grid, (wide ? 16 : kTileWarps) * 32, smem, st>>>(P);
     } else {
         rerank_global_kernel<S><<<grid, 128, 0, st>>>(P);
     }
