@@ -350,8 +350,9 @@ int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, in
  * framework's caching allocator, a fixed arena) a fresh allocation can fail
  * part-way through a run.  bm_match_static needs no context and calls no
  * cudaMalloc, cudaFree or other allocating routine: every intermediate
- * buffer (bf16 operand planes, patch norms, float32 candidate pool, status
- * word, counters) is carved from one array in device memory of
+ * buffer (bf16 operand planes, patch norms, float32 candidate pool, the
+ * column-part lists of the classes that need them, status word, counters)
+ * is carved from one array in device memory of
  * BM_STATIC_SCRATCH_BYTES (16 MiB).  The array belongs to a module of the
  * library that CUDA loads lazily (its default): the first symbol lookup on a
  * device reserves it -- bm_static_init(), or else the first bm_match_static
@@ -364,7 +365,7 @@ int bm_nlm(bm_ctx* ctx, const void* img, int H, int W, int C, bm_dtype dtype, in
  * whose working set (bm_static_scratch_bytes) exceeds the array returns
  * BM_ERR_TOO_LARGE with nothing launched; bm_last_error(NULL) says how many
  * bytes it needed.  For reference, a 512 x 512 float32 image with patch 8,
- * stride 3, window 39, K 16 needs about 13.5 MB.
+ * stride 3, window 39, K 16 needs about 11.7 MB.
  *
  * Set-up: the first call on a device (the current device) looks up the
  * array's address there with cudaGetSymbolAddress.  Make that first call
