@@ -7,6 +7,10 @@ The rule: L = K + 8 rounded up to 8 by default; four or eight channels keep
 K + 16 (K <= 40) or K + 24; one channel at windows of 45 or more keeps K + 16
 for K <= 24 and for K > 40 -- each only when the larger pool leaves the
 tensor-core geometry no worse (the config-3 class keeps K + 8).
+
+Also host-only: every class of the serving mix has a tensor-core geometry
+(column parts where the staged tile does not fit whole), and the static
+entry point's scratch carries the same part lists as a context workspace.
 """
 import pytest
 
@@ -65,3 +69,28 @@ def test_uint8_jobs_have_no_pool():
     a = B.bm_workspace_bytes(512, 512, 1, B.BM_U8, 8, 39, 3, 16)
     b = B.bm_workspace_bytes(512, 512, 1, B.BM_F32, 8, 39, 3, 16)
     assert 0 < a < b
+
+
+def test_every_serving_class_runs_on_tensor_cores():
+    """Every class of the serving mix (uint8 / float32, one or four channels,
+    patch 8 at stride 3 or 7 at stride 4, window 39 or 61, K 16 / 32 / 70)
+    has a tensor-core geometry (a workspace; the direct kernel needs none),
+    at the mix's smallest and largest sides and an uneven one."""
+    for dt in (B.BM_U8, B.BM_F32):
+        for C in (1, 4):
+            for p, s in ((8, 3), (7, 4)):
+                for win in (39, 61):
+                    for K in (16, 32, 70):
+                        for H, W in ((128, 128), (2048, 2048), (1000, 333)):
+                            assert B.bm_workspace_bytes(H, W, C, dt, p, win, s, K) > 0, (dt, C, p, win, K, H, W)
+                            assert 1 <= B.bm_window_split(H, W, C, dt, p, win, s, K) <= 4
+
+
+def test_column_part_lists_in_static_scratch():
+    # a column-part class's static scratch holds its part lists on top of the pool
+    parts = B.bm_window_split(512, 512, 4, B.BM_F32, 8, 61, 3, 32)
+    assert parts == 2
+    ws = B.bm_workspace_bytes(512, 512, 4, B.BM_F32, 8, 61, 3, 32)
+    st = B.bm_static_scratch_bytes(512, 512, 4, B.BM_F32, 8, 61, 3, 32)
+    # both layouts carry the same operand, norm, pool and part-list arrays
+    assert abs(ws - st) <= 512
